@@ -1,0 +1,265 @@
+"""Benchmark of the coupled phase-field / surfactant / flow LBM step on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+
+Workload (default): the sheared sessile drop (top wall at u_w = 0.01, 90 deg contact
+angle, psi0 = 0.02, solid-gas adsorption 0.5, tau = 0.8, eps = 4, FP32) on a
+4096 x 2048 grid with R = 480, i.e. the 512 x 256 shear configuration scaled to the
+domain size the throughput target is quoted on.  One step = one time step of the whole
+coupled update over the whole grid (one kernel launch).  The 4096 x 2048 state
+(2.2 GB) is far larger than the 126 MB L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  Metric: MLUPS (million lattice-node updates per
+second, whole job).  Under torchrun with N > 1 every rank steps its own replica of the
+workload ('replicas only': the single-domain path has no multi-GPU exchange here).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+BYTES_PER_CELL = {"fp32": 264, "fp16": 132, "bf16": 132}   # algorithmic bytes per cell update
+DTYPE = {"fp32": "f32", "fp16": "f16-storage/f32-compute", "bf16": "bf16-storage/f32-compute"}
+
+
+def shear_case(nx, ny, precision="fp32"):
+    R = 480.0 * ny / 2048.0
+    return dict(nx=nx, ny=ny, R=R, xc=nx / 4.0, theta=90.0, psi0=0.02, beta_sg=0.5, beta_sl=0.0, u_w=0.01,
+                precision=precision)
+
+
+def init_fields(case):
+    from paper_2609_26332_b300 import inputs
+    pb = inputs.bulk_phi(case["psi0"], 1.0)
+    return inputs.sessile_drop(case["nx"], case["ny"], case["R"], 4.0, xc=case["xc"], phi_b=pb, psi0=case["psi0"])
+
+
+def make_domain(case, stream):
+    from paper_2609_26332_b300 import binding as B
+    p = B.default_params(case["nx"], case["ny"], precision=case["precision"], psi_b=case["psi0"])
+    d = B.Domain(p, stream=stream)
+    d.set_wall(0, case["theta"], case["beta_sg"], case["beta_sl"], 0.0)
+    d.set_wall(1, 90.0, 0.0, 0.0, case["u_w"])
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        j = json.load(open(path))
+        return float(j["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle, as it stands, on a bounded sample: the 512 x 256 shear configuration."""
+    from oracle import Oracle, OracleParams, Wall
+    case = shear_case(512, 256)
+    phi0, psi0 = init_fields(case)
+    p = OracleParams(nx=512, ny=256, psi_b=case["psi0"],
+                     walls=[Wall(case["theta"], case["beta_sg"], case["beta_sl"], 0.0), Wall(90.0, 0, 0, case["u_w"])])
+    o = Oracle(p, phi0, psi0)
+    o.step(1)
+    t = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t < seconds:
+        o.step(1)
+        n += 1
+    dt = time.perf_counter() - t
+    return {"value": 512 * 256 * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"numpy FP64 oracle, 512x256 shear configuration, {n} steps, 1 thread"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import Oracle, OracleParams, Wall
+    case = shear_case(512, 256)
+    phi0, psi0 = init_fields(case)
+    p = OracleParams(nx=512, ny=256, psi_b=case["psi0"],
+                     walls=[Wall(case["theta"], case["beta_sg"], case["beta_sl"], 0.0), Wall(90.0, 0, 0, case["u_w"])])
+    o = Oracle(p, phi0, psi0)
+    o.step(args.warmup)
+    t = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t
+    v = 512 * 256 * args.steps / dt / 1e6
+    sample = f"numpy FP64 oracle on the 512x256 shear configuration (bounded sample of the workload), 1 thread"
+    print(json.dumps({
+        "impl": "reference", "metric": "coupled-step MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "shear-drop 512x256 (oracle sample of the 4096x2048 shear workload)"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--nx", type=int, default=4096)
+    ap.add_argument("--ny", type=int, default=2048)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2609_26332_b300 import build as _build
+    _build.build()
+    from paper_2609_26332_b300 import binding as B
+
+    case = shear_case(args.nx, args.ny, args.precision)
+    cells = args.nx * args.ny
+    stream = torch.cuda.current_stream()
+    phi0, psi0 = init_fields(case)
+    d = make_domain(case, stream)
+    d.init_fields(phi0, psi0)
+    d.step(args.warmup)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop() if sampler else None
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    tot = d.read_totals(check=False)
+
+    # end to end through the C ABI with host buffers: upload, step, read back
+    pin_phi = torch.from_numpy(phi0).pin_memory().numpy()
+    pin_psi = torch.from_numpy(psi0).pin_memory().numpy()
+    outs = {k: torch.empty((args.ny, args.nx), dtype=torch.float64).pin_memory().numpy()
+            for k in ("phi", "psi", "ux", "uy", "p")}
+    import ctypes
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    d.init_fields(pin_phi, pin_psi)
+    d.step(args.steps)
+    B.lib.slbm_read_fields(d._h, *[outs[k].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                                   for k in ("phi", "psi", "ux", "uy", "p")])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        per_launch_s = ms_max / 1e3 / args.steps
+        achieved = BYTES_PER_CELL[args.precision] * cells / per_launch_s / 1e9
+        value = world * cells * args.steps / (ms_max / 1e3) / 1e6
+        line = {
+            "metric": "coupled-step MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"shear-drop {args.nx}x{args.ny} R={case['R']:.0f} {args.precision} "
+                                   "(512x256 shear configuration scaled to the 4096x2048 target size)",
+                       "nx": args.nx, "ny": args.ny, "cells": cells, "parallelism": f"replicas{world}",
+                       "l2": "state 2.2 GB >> 126 MB L2, no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind, "bytes_per_cell": BYTES_PER_CELL[args.precision]},
+            "e2e": {"value": world * cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": 16 * cells / args.steps, "d2h_bytes_per_step": 40 * cells / args.steps},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "totals": {"psi_total": tot["psi_total"], "lambda_phi": tot["lambda_phi"],
+                       "range_count": tot["range_count"]},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    d.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

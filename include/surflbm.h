@@ -1,0 +1,165 @@
+/*
+ * surflbm.h - C ABI of the B300 (sm_103a) solver for the coupled phase-field /
+ * surfactant / flow lattice Boltzmann model of Huang, Chai, Liu and Huang,
+ * "A thermodynamically consistent and conservative phase-field model for surfactant
+ * contact line dynamics with solid adsorption".
+ *
+ * One call of slbm_step advances the three coupled D2Q9 MRT lattice Boltzmann
+ * equations of Sec. 3 by one or more time steps on the GPU:
+ *   - the conservative Allen-Cahn equation for the phase field phi with the weighted
+ *     nonlinear Lagrange multiplier lambda_phi = int h' mu / int h'^2 (Eqs. AC_phi, eq15),
+ *   - the Allen-Cahn equation for the surfactant psi with the linear constraint
+ *     mubar_psi = mean(mu_psi) (Eq. AC_psi),
+ *   - the incompressible Navier-Stokes flow driven by F = -phi grad mu_phi - psi grad mu_psi
+ *     (Eqs. eqns, eq_Fs0),
+ * with the wetting and solid-adsorption boundary conditions of Eq. boundary.
+ *
+ * Geometry (lattice units, dx = dt = 1): nx x ny nodes, node (i, j) at x = i,
+ * y = j + 1/2; x is periodic; solid walls lie at y = 0 (wall 0, bottom) and y = ny
+ * (wall 1, top).  Host arrays are row-major [ny][nx] doubles (index j * nx + i).
+ *
+ * Conventions: every call returns an slbm_status; nothing throws across the ABI.
+ * The library owns all device state of a domain (allocated in slbm_create_domain);
+ * the caller owns every host buffer it passes, which the library only reads or writes
+ * during the call.  Work is queued on the CUDA stream given at creation (NULL = the
+ * legacy default stream); calls that return data synchronise that stream.  A domain
+ * must not be used from two threads at once.  After SLBM_ECUDA the domain should be
+ * destroyed.  slbm_last_error returns a message owned by the domain (or a static
+ * message for a NULL domain) valid until the next call on that domain.
+ */
+#ifndef SURFLBM_H
+#define SURFLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SLBM_OK = 0,
+    SLBM_EINVAL = 1,    /* bad argument or parameter                                  */
+    SLBM_ENOMEM = 2,    /* device allocation failed                                   */
+    SLBM_ECUDA = 3,     /* a CUDA runtime call failed                                 */
+    SLBM_EUNSTABLE = 4, /* a reduced quantity became non-finite or a population left  */
+                        /* the fixed-point exchange range (the run has diverged)      */
+    SLBM_ESTATE = 5     /* call not valid in the current state (e.g. fields not set)  */
+} slbm_status;
+
+/* Storage of the moving populations and of the source-term history.
+ * FP32: 32-bit floats.  FP16DEV / BF16DEV: 16-bit floats holding deviations from
+ * the rest equilibrium w_i m of each scalar set (and the flow populations, whose
+ * rest equilibrium at zero reference pressure is 0).  In every mode the conserved
+ * zeroth moments are kept in 48-bit float-float, collisions are done in FP32 and
+ * global integrals in FP64. */
+typedef enum { SLBM_FP32 = 0, SLBM_FP16DEV = 1, SLBM_BF16DEV = 2 } slbm_precision;
+
+/* h_phi of Eq. conservation: nonlinear h = 1/2 + g(phi) (Eq. AC_phi, the paper's
+ * model) or linear h = phi (the classical constraint it is compared with). */
+typedef enum { SLBM_CONSTRAINT_NONLINEAR = 0, SLBM_CONSTRAINT_LINEAR = 1 } slbm_constraint;
+
+/* lambda_phi: PAPER = Eq. eq15, lambda = S1 / S2.  TARGET = (S1 + (H0 - H) / M_phi) / S2,
+ * which feeds back the discrete drift of H = sum h_phi(phi) away from its initial
+ * value H0 (the paper's identity holds for the continuous equation only). */
+typedef enum { SLBM_MULT_PAPER = 0, SLBM_MULT_TARGET = 1 } slbm_multiplier;
+
+typedef struct {
+    int nx, ny;              /* grid, nx >= 1, ny >= 2                                  */
+    double tau_f;            /* flow relaxation time of the liquid, 1/s2^1 (> 0.5)       */
+    double tau_f_gas;        /* of the gas; <= 0 means tau_f                            */
+    double tau_g, tau_h;     /* phase field 1/s1^2, surfactant 1/s1^3 (> 0.5)           */
+    /* remaining MRT rates, (s0, s1, s3, s4) for the flow and (s0, s2, s3, s4) for the
+     * scalars; 0 means equal to the field's main rate (all 0: BGK)                   */
+    double mrt_f[4], mrt_g[4], mrt_h[4];
+    double sigma;            /* clean gas-liquid tension sigma_gl,0 (>= 0)               */
+    double eps;              /* interface thickness parameter epsilon (> 0)              */
+    double Ex, Pi;           /* W = 4 beta / Ex (Ex <= 0: W = 0), k_B T = 4 beta Pi      */
+    double M_phi;            /* used only when kappa = 0; else M_phi kappa = eta c_s^2 (tau_g - 1/2) */
+    double M_psi;            /* surfactant mobility; M_0 = eta c_s^2 (tau_h - 1/2) - M_psi lambda_s */
+    double eta_phi, eta_psi; /* equilibrium parameters of Sec. 3 (paper leaves them free; 1) */
+    double lambda_s;         /* < 0: kappa / 2 (Sec. 2.1)                                */
+    double psi_b;            /* reference bulk surfactant for phi_b                     */
+    double phi_b;            /* <= 0: sqrt(1 - W psi_b / (4 beta (1 - psi_b))) (Sec. 2.2) */
+    double rho_l, rho_g;     /* densities of liquid and gas                             */
+    double Gx, Gy;           /* body-force density G                                    */
+    int constraint;          /* slbm_constraint                                         */
+    int multiplier;          /* slbm_multiplier                                         */
+    int precision;           /* slbm_precision                                          */
+    int psi_on;              /* 0: surfactant transport disabled (psi == 0)             */
+} slbm_params;
+
+/* Quantities reduced in FP64 over the whole grid at one time level. */
+typedef struct {
+    long long step;          /* number of completed time steps                          */
+    double Q_phi;            /* sum of Q(phi) = 2 h_phi(phi) - 1 (Eq. conservation_Q)   */
+    double H;                /* sum h_phi(phi): the conserved measure of the constraint */
+    double phi_total;        /* sum phi                                                 */
+    double psi_total;        /* sum psi (conserved by Eq. AC_psi)                       */
+    double lambda_phi;       /* Lagrange multiplier of Eq. eq15 at this time level      */
+    double mubar_psi;        /* mean surfactant chemical potential (Eq. AC_psi)         */
+    double kinetic;          /* sum rho |u|^2 / 2                                       */
+    double S1, S2;           /* sum h' mu_phi, sum h'^2                                 */
+    long long clamp_count;   /* cells whose psi was clamped inside ln(psi / (1 - psi))  */
+    long long range_count;   /* non-finite values or fixed-point range violations       */
+} slbm_totals;
+
+typedef struct slbm_domain slbm_domain;
+
+/* Sets every field of *p to the documented defaults for an nx x ny grid
+ * (tau = 0.8 everywhere, sigma = 0.01, eps = 4, Ex = 1, Pi = 0.18407, M_psi = 0.5,
+ * eta = 1, derived lambda_s and phi_b, unit densities, no body force, nonlinear
+ * constraint, paper multiplier, FP32, surfactant on). */
+void slbm_default_params(slbm_params* p, int nx, int ny);
+
+/* Validates *p and allocates the device state.  stream: a cudaStream_t or NULL.
+ * Errors: EINVAL (bad parameters; message in slbm_last_error(NULL)), ENOMEM, ECUDA.
+ * On error *out is set to NULL. */
+slbm_status slbm_create_domain(const slbm_params* p, void* stream, slbm_domain** out);
+
+/* Sets one wall (0 bottom, 1 top): clean contact angle theta0 in degrees (0, 180),
+ * solid adsorption elasticities beta_sg, beta_sl >= 0 of Eq. langmuir, and the
+ * tangential wall speed u_x.  sigma_sg0, sigma_sl0 follow from Young's relation and
+ * sigma_sg0 + sigma_sl0 = 16 sigma / 15 (Sec. 4.4).  Default: 90 deg, 0, 0, 0.
+ * Takes effect from the next step; call before slbm_init_fields for a moving wall so
+ * that the initial state is at rest in the wall frame as documented there. */
+slbm_status slbm_set_walls(slbm_domain* d, int wall, double theta0_deg,
+                           double beta_sg, double beta_sl, double u_x);
+
+/* Copies the initial fields (host, ny*nx doubles each; psi may be NULL when psi_on = 0)
+ * and sets the state to the equilibria at rest (u = 0, p = 0) of those fields at
+ * step 0, as the pre-collision populations of time 0.  Resets the step counter. */
+slbm_status slbm_init_fields(slbm_domain* d, const double* phi, const double* psi);
+
+/* Queues nsteps >= 0 time steps on the domain's stream (asynchronous).  Returns the
+ * status of previously completed work only when it is already known (ECUDA on a
+ * launch failure); divergence is reported by slbm_read_totals.  ESTATE if the
+ * fields were never initialised. */
+slbm_status slbm_step(slbm_domain* d, long long nsteps);
+
+/* Computes phi, psi, u_x, u_y and p at the current time level (the moments of the
+ * current populations, Sec. 3) and copies them to the host arrays (ny*nx doubles
+ * each; any pointer may be NULL).  Synchronises the stream. */
+slbm_status slbm_read_fields(slbm_domain* d, double* phi, double* psi,
+                             double* ux, double* uy, double* p);
+
+/* Reduces the totals at the current time level into *t.  Synchronises.
+ * Returns EUNSTABLE (with *t filled) when range_count > 0 or a total is non-finite. */
+slbm_status slbm_read_totals(slbm_domain* d, slbm_totals* t);
+
+/* Bytes of device memory the domain holds. */
+size_t slbm_device_bytes(const slbm_domain* d);
+
+/* Releases everything the domain owns (NULL is a no-op). */
+void slbm_destroy(slbm_domain* d);
+
+/* Message describing the last error on d (or of the last create when d is NULL). */
+const char* slbm_last_error(const slbm_domain* d);
+
+/* Library version string. */
+const char* slbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SURFLBM_H */
