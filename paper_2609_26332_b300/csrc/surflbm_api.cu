@@ -82,6 +82,7 @@ struct slbm_domain {
     double wall_theta[2] = {90.0, 90.0}, wall_bsg[2] = {0, 0}, wall_bsl[2] = {0, 0}, wall_u[2] = {0, 0};
     long long N = 0;
     dim3 grid;
+    long long total = 0;   // strips * ny, the rows the CTAs share out
     int cur = 0;
     long long n = 0;
     bool initialised = false;
@@ -114,7 +115,7 @@ slbm_status cuda_fail(slbm_domain* d, cudaError_t e, const char* what) {
 std::string validate(const slbm_params* p) {
     if (!p) return "params is NULL";
     if (p->nx < 1 || p->ny < 2) return "need nx >= 1 and ny >= 2";
-    if ((long long)p->nx * p->ny > (1LL << 31)) return "grid larger than 2^31 cells";
+    if ((long long)p->nx * p->ny > (1LL << 28)) return "grid larger than 2^28 cells";
     if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5) || !(p->tau_h > 0.5)) return "relaxation times must exceed 0.5";
     if (p->tau_f_gas > 0 && !(p->tau_f_gas > 0.5)) return "tau_f_gas must exceed 0.5";
     for (int i = 0; i < 4; ++i)
@@ -191,7 +192,7 @@ StepArgs<T> make_args(slbm_domain* d, bool diag) {
     StepArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     const int i = d->cur, o = d->cur ^ 1;
-    a.nx = d->p.nx; a.ny = d->p.ny; a.N = d->N;
+    a.nx = d->p.nx; a.ny = d->p.ny; a.N = d->N; a.total = d->total;
     a.f_in = (const T*)d->f[i]; a.gd_in = (const T*)d->gd[i]; a.gm_in = d->gm[i];
     a.hd_in = (const T*)d->hd[i]; a.hm_in = d->hm[i]; a.php_in = d->php[i];
     a.f_out = (T*)d->f[o]; a.gd_out = (T*)d->gd[o]; a.gm_out = d->gm[o];
@@ -211,11 +212,59 @@ StepArgs<T> make_args(slbm_domain* d, bool diag) {
 }
 
 template <class T>
+cudaError_t prepare_kernels() {
+    static cudaError_t done = cudaErrorNotReady;
+    if (done == cudaErrorNotReady) {
+        const int sm = (int)smem_bytes<T>();
+        done = cudaFuncSetAttribute(step_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(step_kernel<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(step_kernel<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (done == cudaSuccess)
+            done = cudaFuncSetAttribute(step_kernel<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    }
+    return done;
+}
+
+template <class T>
 cudaError_t launch_step(slbm_domain* d, bool diag) {
+    cudaError_t e = prepare_kernels<T>();
+    if (e != cudaSuccess) return e;
     StepArgs<T> a = make_args<T>(d, diag);
-    if (diag) step_kernel<T, true><<<d->grid, NTHREADS, 0, d->stream>>>(a);
-    else step_kernel<T, false><<<d->grid, NTHREADS, 0, d->stream>>>(a);
+    // uniform density and viscosity (the common case) drop every density-gradient term
+    const bool var = a.P.var_nu || a.P.rho_l != a.P.rho_g;
+    const size_t sm = smem_bytes<T>();
+    if (diag) {
+        if (var) step_kernel<T, true, true><<<d->grid, NTHREADS, sm, d->stream>>>(a);
+        else step_kernel<T, true, false><<<d->grid, NTHREADS, sm, d->stream>>>(a);
+    } else {
+        if (var) step_kernel<T, false, true><<<d->grid, NTHREADS, sm, d->stream>>>(a);
+        else step_kernel<T, false, false><<<d->grid, NTHREADS, sm, d->stream>>>(a);
+    }
     return cudaGetLastError();
+}
+
+template <class T>
+int resident_ctas_per_sm() {
+    int n = 0;
+    if (prepare_kernels<T>() != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<T, false, false>, NTHREADS, smem_bytes<T>()) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+// Persistent grid: one CTA per resident slot, unless the grid is so small that a CTA
+// would get fewer than 16 strip rows (the 6-row prologue is paid per piece).
+int choose_ctas(slbm_domain* d, int ctas_per_sm) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long slots = (long long)sms * ctas_per_sm;
+    long long n = (d->total + 15) / 16;
+    if (n > slots) n = slots;
+    if (n < 1) n = 1;
+    return (int)n;
 }
 
 cudaError_t launch(slbm_domain* d, bool diag) {
@@ -281,8 +330,17 @@ slbm_status slbm_create_domain(const slbm_params* p, void* stream, slbm_domain**
     d->p = *p;
     d->stream = (cudaStream_t)stream;
     d->N = (long long)p->nx * p->ny;
-    d->grid = dim3((unsigned)((p->nx + TX - 1) / TX), (unsigned)((p->ny + TY - 1) / TY));
     derive(d);
+    {
+        int per_sm = 1;
+        switch (p->precision) {
+            case SLBM_FP16DEV: per_sm = resident_ctas_per_sm<__half>(); break;
+            case SLBM_BF16DEV: per_sm = resident_ctas_per_sm<__nv_bfloat16>(); break;
+            default: per_sm = resident_ctas_per_sm<float>(); break;
+        }
+        d->total = (long long)((p->nx + TX - 1) / TX) * p->ny;
+        d->grid = dim3((unsigned)choose_ctas(d, per_sm));
+    }
     const size_t es = elem_size(p->precision);
     const size_t N = (size_t)d->N;
     slbm_status s = SLBM_OK;

@@ -73,6 +73,7 @@ template <class T> struct Stor;
 template <> struct Stor<float> {
     static constexpr float kScale = 1.0f, kInv = 1.0f;
     static __device__ __forceinline__ float ld(const float* p, long long i) { return __ldg(p + i); }
+    static __device__ __forceinline__ float lds(const float* p, int i) { return p[i]; }
     static __device__ __forceinline__ float rnd(float v) { return v; }
     static __device__ __forceinline__ void st(float* p, long long i, float v) { p[i] = v; }
 };
@@ -82,6 +83,7 @@ template <> struct Stor<__half> {
     static __device__ __forceinline__ float ld(const __half* p, long long i) {
         return __half2float(__ldg(p + i)) * kInv;
     }
+    static __device__ __forceinline__ float lds(const __half* p, int i) { return __half2float(p[i]) * kInv; }
     static __device__ __forceinline__ float rnd(float v) { return __half2float(__float2half_rn(v * kScale)) * kInv; }
     static __device__ __forceinline__ void st(__half* p, long long i, float v) { p[i] = __float2half_rn(v * kScale); }
 };
@@ -90,6 +92,7 @@ template <> struct Stor<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p, long long i) {
         return __bfloat162float(__ldg(p + i));
     }
+    static __device__ __forceinline__ float lds(const __nv_bfloat16* p, int i) { return __bfloat162float(p[i]); }
     static __device__ __forceinline__ float rnd(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, long long i, float v) { p[i] = __float2bfloat16_rn(v); }
 };

@@ -1,31 +1,58 @@
 // The fused stream-collide kernel of the coupled LBM step and its helpers.
 //
-// One launch advances every cell by one time step (pull scheme, Sec. 3):
-//   phase 1  pull the two scalar sets on the tile plus a 2-node ring, giving
-//            phi and psi exactly in float-float (fixed-point exchange);
-//   phase 2  wall ghost rows (Eq. boundary) and the chemical potentials
-//            mu_phi, mu_psi (Eqs. eq_muphi, eq_mupsi) on the tile plus a 1-node ring;
-//   phase 3  per interior cell: force (Eq. eq_Fs0), flow pull with bounce-back walls,
-//            velocity and pressure, equilibria, sources and the MRT/BGK collisions of
-//            all three sets; store; FP64 block partials of the global integrals;
-//   tail     the last block to finish reduces the partials in a fixed order and
-//            resolves lambda_phi (Eq. eq15) and mubar_psi (Eq. AC_psi).
+// Each CTA owns a strip of TX columns and a segment of rows, and marches up the
+// segment RB rows at a time through a software pipeline kept in shared memory rings
+// of 8 rows (row y lives in slot y & 7):
+//   stage K    for every source node of the next rows, the eight populations it sends,
+//              converted once to 32-bit fixed point (both scalar sets);
+//   stage PHI  pull: phi, psi of the rows two ahead, exactly, as float-float
+//              (m~ + received - sent, an integer sum that telescopes over the grid);
+//   stage MU   chemical potentials mu_phi, mu_psi (Eqs. eq_muphi, eq_mupsi) one row ahead,
+//              with the wall ghost rows of Eq. boundary;
+//   stage COLLIDE  per cell: force (Eq. eq_Fs0), flow pull with bounce-back walls, u, p,
+//              equilibria, sources and the MRT/BGK collisions of the three sets (Sec. 3),
+//              stores, and the FP64-reduced global integrals.
+// The last CTA to finish reduces the block partials in a fixed order and resolves
+// lambda_phi (Eq. eq15) and mubar_psi (Eq. AC_psi).
 //
 // lambda^n and mubar^n enter the step-n populations only as w_i * (scalar at the node)
 // in the source w_i (R + dt/2 dR/dt); that term lands entirely on the stored zeroth
-// moment, so it is applied by the next launch when it pulls (a deferred correction
+// moment, so the next launch applies it when it pulls (a deferred correction,
 // algebraically identical to applying it in this step) and no grid-wide barrier is needed.
 #pragma once
+#include <type_traits>
 #include "surflbm_device.cuh"
 
 namespace slbm {
 
-constexpr int TX = 32;          // tile width (cells)
-constexpr int TY = 16;          // tile height
-constexpr int NTHREADS = 256;   // 32 x 8 threads, two cells each
-constexpr int R2X = TX + 4, R2Y = TY + 4;
-constexpr int R1X = TX + 2, R1Y = TY + 2;
-constexpr int NPART = 9;        // doubles per block partial
+constexpr int TX = 64;           // strip width (cells)
+constexpr int RB = 4;            // rows per pipeline iteration
+constexpr int NTHREADS = TX * RB;
+constexpr int RING = 8;          // ring depth (rows)
+constexpr int KX = TX + 6;       // columns of the fixed-point ring (3-node halo)
+constexpr int PX = TX + 4;       // columns of the phi / psi ring (2-node halo)
+constexpr int MX = TX + 2;       // columns of the mu ring (1-node halo)
+constexpr int NPART = 9;         // doubles per block partial
+
+// Raw source rows are staged with cp.async through a 16-byte aligned window of WW
+// columns starting at x0 - WOFF (covers the K-ring columns x0 - 3 .. x0 + TX + 2).
+constexpr int WOFF = 8;
+constexpr int WW = TX + 16;
+
+// dynamic shared memory layout (bytes)
+constexpr size_t SM_K = 2ull * 8 * RING * KX * sizeof(int);      // fixed-point populations
+constexpr size_t SM_MT = 2ull * RING * KX * sizeof(float2);      // m~ of every ring node
+constexpr size_t SM_P = 4ull * RING * PX * sizeof(float);        // phi, psi (float-float)
+constexpr size_t SM_M = 2ull * RING * MX * sizeof(float);        // mu_phi, mu_psi
+template <class T> struct Staging {
+    static constexpr size_t D_ROW = 16ull * WW * sizeof(T);      // 16 deviation planes
+    static constexpr size_t M_ROW = 2ull * WW * sizeof(float2);   // two zeroth-moment planes
+    static constexpr size_t P_ROW = 1ull * WW * sizeof(float);    // phi of the previous step
+    static constexpr size_t ROW = D_ROW + M_ROW + P_ROW;
+    static constexpr size_t BUF = RB * ROW;
+    static constexpr size_t BYTES = 2 * BUF;
+};
+template <class T> constexpr size_t smem_bytes() { return SM_K + SM_MT + SM_P + SM_M + Staging<T>::BYTES; }
 
 // indices of the block partials / reduced quantities
 enum { P_S1 = 0, P_S2, P_S3, P_Q, P_PHI, P_PSI, P_KIN, P_CLAMP, P_RANGE };
@@ -53,6 +80,7 @@ template <class T>
 struct StepArgs {
     int nx, ny;
     long long N;
+    long long total;              // strips * ny: the strip-major rows shared out among the CTAs
     // state in (post-collision of the previous step) and out
     const T* f_in; const T* gd_in; const float2* gm_in; const T* hd_in; const float2* hm_in; const float* php_in;
     T* f_out; T* gd_out; float2* gm_out; T* hd_out; float2* hm_out; float* php_out;
@@ -62,7 +90,7 @@ struct StepArgs {
     const Rec* rec_prev;          // time level n-1 (zeros before the first step)
     Rec* rec_out;                 // time level n
     int first;                    // this is the first step after initialisation
-    // DIAG outputs (device, double)
+    // DIAG outputs (device, double; may be null)
     double* o_phi; double* o_psi; double* o_ux; double* o_uy; double* o_p;
     Phys P;
 };
@@ -71,63 +99,36 @@ __device__ __forceinline__ int wrapx(int x, int nx) {
     x %= nx;
     return x < 0 ? x + nx : x;
 }
+// x within [-nx, 2nx): one conditional correction
+__device__ __forceinline__ int wrap1(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// c_k . (ax, ay) with the zero lattice components folded away at compile time (IEEE
+// arithmetic may not drop 0 * x, so the generic form would pay for every zero)
+__device__ __forceinline__ float cdot(int k, float ax, float ay) {
+    const int cx = CXk(k), cy = CYk(k);
+    if (cx == 0 && cy == 0) return 0.0f;
+    if (cy == 0) return cx > 0 ? ax : -ax;
+    if (cx == 0) return cy > 0 ? ay : -ay;
+    const float t = cx > 0 ? ax : -ax;
+    return cy > 0 ? t + ay : t - ay;
+}
+// acc + sgn * v for a compile-time integer sign in {-1, 0, 1}
+__device__ __forceinline__ float addc(float acc, int sgn, float v) {
+    return sgn == 0 ? acc : (sgn > 0 ? acc + v : acc - v);
+}
 
 // h_phi'(phi) = g'(phi) = 3/(4 phi_b) (1 - phi^2/phi_b^2), or 1 for the linear constraint
 __device__ __forceinline__ float hprime(float phi, const Phys& P) {
     if (P.linear) return 1.0f;
-    float u = phi * P.inv_phi_b;
-    return 0.75f * P.inv_phi_b * (1.0f - u * u);
-}
-
-// fixed-point value of the population leaving `node` in direction k:
-// v = d_k(node) + w_k * hi(m~(node)), converted once with round-to-nearest
-__device__ __forceinline__ int kval(float d, float w, float mh, float scale, int& range) {
-    float v = __fadd_rn(d, __fmul_rn(w, mh));
-    float sv = __fmul_rn(v, scale);
-    range |= !(fabsf(sv) < 2147483000.0f);
-    return __float2int_rn(sv);
-}
-
-// m~ = m + correction of the deferred multiplier term of the previous step
-template <bool PHISET>
-__device__ __forceinline__ ff mtilde(const float2* __restrict__ m, const float* __restrict__ php, long long c,
-                                     float qcoef, ff cuni, const Phys& P) {
-    float2 mv = __ldg(m + c);
-    ff r = {mv.x, mv.y};
-    if (PHISET) {
-        if (qcoef != 0.0f) r = ff_add_f(r, __fmul_rn(qcoef, hprime(__ldg(php + c), P)));
-    } else {
-        r = ff_add(r, cuni);
-    }
-    return r;
-}
-
-// Pull one scalar set at (x, y): returns the zeroth moment exactly (float-float) and,
-// if Kin != nullptr, the eight received fixed-point populations.  Walls: specular.
-template <class T, bool PHISET>
-__device__ __forceinline__ ff pull_scalar(const T* __restrict__ d, const float2* __restrict__ m,
-                                          const float* __restrict__ php, int x, int y, int nx, int ny,
-                                          long long N, float qcoef, ff cuni, const Phys& P, int* Kin,
-                                          int& range) {
-    const float scale = PHISET ? (float)(1u << SFIX_PHI) : 2147483648.0f;
-    const float inv_scale = 1.0f / scale;
-    const long long c = (long long)y * nx + x;
-    ff mself = mtilde<PHISET>(m, php, c, qcoef, cuni, P);
-    int ksum = 0;
-#pragma unroll
-    for (int k = 1; k < 9; ++k) {
-        ksum -= kval(Stor<T>::ld(d, (long long)(k - 1) * N + c), Wk(k), mself.hi, scale, range);
-        int sy = y - CYk(k);
-        int sx = wrapx(x - CXk(k), nx);
-        int kk = k;
-        if (sy < 0 || sy >= ny) { sy = y; kk = MIRYk(k); }
-        long long sc = (long long)sy * nx + sx;
-        ff ms = mtilde<PHISET>(m, php, sc, qcoef, cuni, P);
-        int kin = kval(Stor<T>::ld(d, (long long)(kk - 1) * N + sc), Wk(kk), ms.hi, scale, range);
-        ksum += kin;
-        if (Kin) Kin[k] = kin;
-    }
-    return ff_add(mself, fixed_to_ff(ksum, inv_scale));
+    float u = __fmul_rn(phi, P.inv_phi_b);
+    return __fmul_rn(__fmul_rn(0.75f, P.inv_phi_b), __fsub_rn(1.0f, __fmul_rn(u, u)));
 }
 
 // wetting / adsorption ghost values (Eq. boundary, reading c2): phi_G = phi_w - (df_w/dphi)/kappa,
@@ -159,6 +160,7 @@ __device__ __forceinline__ ff warp_sum_ff(ff v) {
 template <class T>
 __device__ void finish_reduction(ff (&acc)[NPART], const StepArgs<T>& A, bool diag) {
     __shared__ double s_w[NPART][NTHREADS / 32];
+    __shared__ double s_tot[NPART];
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -183,8 +185,7 @@ __device__ void finish_reduction(ff (&acc)[NPART], const StepArgs<T>& A, bool di
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // fixed-order reduction: warp q sums quantity q (and q + 8), lanes stride the blocks
-    __shared__ double s_tot[NPART];
+    // fixed-order reduction: warp w sums quantities w, w + 8, lanes stride the blocks
     for (int q = warp; q < NPART; q += NTHREADS / 32) {
         double s = 0.0;
         for (int b = lane; b < nblocks; b += 32) s += ((volatile double*)A.partials)[(long long)b * NPART + q];
@@ -221,187 +222,396 @@ __device__ void finish_reduction(ff (&acc)[NPART], const StepArgs<T>& A, bool di
     }
 }
 
+// ring accessors
+#define KR(s, k, y, col) sK[(((s) * 8 + ((k) - 1)) * RING + ((y) & (RING - 1))) * KX + (col)]
+#define MT(s, y, col) sMT[((s) * RING + ((y) & (RING - 1))) * KX + (col)]
+#define PH(y, col) sPh[((y) & (RING - 1)) * PX + (col)]
+#define PL(y, col) sPl[((y) & (RING - 1)) * PX + (col)]
+#define SH(y, col) sSh[((y) & (RING - 1)) * PX + (col)]
+#define SL(y, col) sSl[((y) & (RING - 1)) * PX + (col)]
+#define MU(y, col) sMu[((y) & (RING - 1)) * MX + (col)]
+#define MP(y, col) sMp[((y) & (RING - 1)) * MX + (col)]
+
+// received fixed-point population in direction k at (row y, K-ring column kc); walls: specular
+__device__ __forceinline__ int k_in(const int* __restrict__ sK, int s, int k, int y, int kc, int ny) {
+    const int sy = y - CYk(k);
+    if (sy < 0 || sy >= ny) return KR(s, MIRYk(k), y, kc - CXk(k));
+    return KR(s, k, sy, kc - CXk(k));
+}
+
+// compile-time loop: f(integral_constant<int, I>) for I in [B, E); the lattice tables
+// then fold to constants in every direction-dependent expression
+template <int I, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I < E) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, E>(static_cast<F&&>(f));
+    }
+}
+
 // ------------------------------------------------------------------- the step
 // DIAG = true: same moments / forces / velocity / pressure, no collision, writes the
 // macroscopic fields and the reduced totals of the current time level.
-template <class T, bool DIAG>
-__global__ void __launch_bounds__(NTHREADS) step_kernel(const StepArgs<T> A) {
+// VARRHO = false: uniform density and viscosity (no density-gradient terms).
+// Work split: the strips x rows of the grid, ordered strip-major, are cut into gridDim.x
+// contiguous ranges of equal length; a CTA marches its range (one or two strip pieces).
+template <class T, bool DIAG, bool VARRHO>
+__global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* sK = (int*)smem;
+    float2* sMT = (float2*)(smem + SM_K);
+    float* sPh = (float*)(smem + SM_K + SM_MT);
+    float* sPl = sPh + RING * PX;
+    float* sSh = sPl + RING * PX;
+    float* sSl = sSh + RING * PX;
+    float* sMu = (float*)(smem + SM_K + SM_MT + SM_P);
+    float* sMp = sMu + RING * MX;
+    unsigned char* sStg = smem + SM_K + SM_MT + SM_P + SM_M;
+    using ST = Staging<T>;
+
     const Phys& P = A.P;
     const int nx = A.nx, ny = A.ny;
     const long long N = A.N;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tid = threadIdx.x;
+    const float sc_phi = (float)(1u << SFIX_PHI), sc_psi = 2147483648.0f;
+    const float isc_phi = 1.0f / sc_phi, isc_psi = 1.0f / sc_psi;
+    const float inv_rho_l = 1.0f / P.rho_l;
 
-    __shared__ float s_ph[R2Y][R2X], s_pl[R2Y][R2X], s_sh[R2Y][R2X], s_sl[R2Y][R2X];
-    __shared__ float s_mu[R1Y][R1X], s_mp[R1Y][R1X];
-    __shared__ float s_gphi[2][R2X], s_gpsi[2][R2X];
-
-    // deferred multiplier terms of time level n-1
+    // deferred multiplier terms of time level n-1 (FP64 only here, once per thread)
     const Rec rp = *A.rec_prev;
     const float qcoef = (float)(rp.a * P.M_phi_d * rp.lam);
-    const double cu_d = rp.a * rp.mpsi_mubar;
     ff cuni;
-    cuni.hi = (float)cu_d;
-    cuni.lo = (float)(cu_d - (double)cuni.hi);
+    {
+        const double cu = rp.a * rp.mpsi_mubar;
+        cuni.hi = (float)cu;
+        cuni.lo = (float)(cu - (double)cuni.hi);
+    }
+    const float lam_half = (float)(0.5 * P.M_phi_d * rp.lam);
+    ff mub_half;
+    {
+        const double hm = -0.5 * rp.mpsi_mubar;
+        mub_half.hi = (float)hm;
+        mub_half.lo = (float)(hm - (double)mub_half.hi);
+    }
     int range = 0;
-
-    // ---------------- phase 1: phi, psi on the tile + 2-ring
-    for (int idx = tid; idx < R2X * R2Y; idx += NTHREADS) {
-        const int lx = idx % R2X, ly = idx / R2X;
-        const int gy = y0 - 2 + ly;
-        if (gy < 0 || gy >= ny) continue;
-        const int gx = wrapx(x0 - 2 + lx, nx);
-        ff ph = pull_scalar<T, true>(A.gd_in, A.gm_in, A.php_in, gx, gy, nx, ny, N, qcoef, cuni, P, nullptr, range);
-        s_ph[ly][lx] = ph.hi;
-        s_pl[ly][lx] = ph.lo;
-        if (P.psi_on) {
-            ff ps = pull_scalar<T, false>(A.hd_in, A.hm_in, A.php_in, gx, gy, nx, ny, N, 0.0f, cuni, P, nullptr, range);
-            s_sh[ly][lx] = ps.hi;
-            s_sl[ly][lx] = ps.lo;
-        } else {
-            s_sh[ly][lx] = 0.0f;
-            s_sl[ly][lx] = 0.0f;
-        }
-    }
-    __syncthreads();
-
-    // ---------------- phase 2a: ghost rows beyond the walls
-    const int lyb = 2 - y0;            // local row of grid row 0
-    const int lyt = ny - 1 - y0 + 2;   // local row of grid row ny-1
-    for (int lx = tid; lx < R2X; lx += NTHREADS) {
-        if (lyb >= 0 && lyb < R2Y) wall_ghost(s_ph[lyb][lx], s_sh[lyb][lx], 0, P, s_gphi[0][lx], s_gpsi[0][lx]);
-        if (lyt >= 0 && lyt < R2Y) wall_ghost(s_ph[lyt][lx], s_sh[lyt][lx], 1, P, s_gphi[1][lx], s_gpsi[1][lx]);
-    }
-    __syncthreads();
-
-    // ---------------- phase 2b: chemical potentials on the tile + 1-ring
-    float clamps = 0.0f;
-    for (int idx = tid; idx < R1X * R1Y; idx += NTHREADS) {
-        const int l1x = idx % R1X, l1y = idx / R1X;
-        const int lx = l1x + 1, ly = l1y + 1;
-        const int gy = y0 - 1 + l1y;
-        if (gy < 0 || gy >= ny) continue;
-        const float phi = s_ph[ly][lx], psi = s_sh[ly][lx];
-        float lapG_phi = 0.0f, lapG_psi = 0.0f;
-#pragma unroll
-        for (int k = 1; k < 9; ++k) {
-            const int ny_ = gy + CYk(k);
-            float vphi, vpsi;
-            if (ny_ < 0) { vphi = s_gphi[0][lx + CXk(k)]; vpsi = s_gpsi[0][lx + CXk(k)]; }
-            else if (ny_ >= ny) { vphi = s_gphi[1][lx + CXk(k)]; vpsi = s_gpsi[1][lx + CXk(k)]; }
-            else { vphi = s_ph[ly + CYk(k)][lx + CXk(k)]; vpsi = s_sh[ly + CYk(k)][lx + CXk(k)]; }
-            lapG_phi += Wk(k) * (vphi - phi);
-            lapG_psi += Wk(k) * (vpsi - psi);
-        }
-        lapG_phi *= 6.0f;
-        lapG_psi *= 6.0f;
-        s_mu[l1y][l1x] = 4.0f * P.beta * (1.0f - psi) * (phi * phi * phi - phi) - P.kappa * lapG_phi + P.W * psi * phi;
-        if (P.psi_on) {
-            float psc = fminf(fmaxf(psi, P.psi_clamp), 1.0f - P.psi_clamp);
-            float om = 1.0f - phi * phi;
-            s_mp[l1y][l1x] = P.kT * logf(psc / (1.0f - psc)) - P.lambda_s * lapG_psi - P.beta * om * om +
-                             0.5f * P.W * phi * phi;
-        } else {
-            s_mp[l1y][l1x] = 0.0f;
-        }
-    }
-    __syncthreads();
-
-    // ---------------- phase 3: interior cells
+    float clamps = 0.0f, s1acc = 0.0f, s2acc = 0.0f, kinacc = 0.0f;
     ff acc[NPART];
 #pragma unroll
     for (int q = 0; q < NPART; ++q) acc[q] = {0.0f, 0.0f};
+    const int nsets = P.psi_on ? 2 : 1;
 
-    const int tx = tid & 31, tyb = tid >> 5;
-#pragma unroll 1
-    for (int sub = 0; sub < 2; ++sub) {
-        const int ty = tyb + 8 * sub;
-        const int gx = x0 + tx, gy = y0 + ty;
-        if (gx >= nx || gy >= ny) continue;
-        const long long c = (long long)gy * nx + gx;
-        const int lx = tx + 2, ly = ty + 2, l1x = tx + 1, l1y = ty + 1;
-        const ff phff = {s_ph[ly][lx], s_pl[ly][lx]};
-        const ff psff = {s_sh[ly][lx], s_sl[ly][lx]};
-        const float phi = phff.hi, psi = psff.hi;
+    int x0 = 0, ys = 0, ye = 0;
+    bool vec = false;
+    constexpr int VEC = (16 / sizeof(T)) > 4 ? (16 / sizeof(T)) : 4;
 
-        // gradients (mirror ghosts for mu and rho), Neumann Laplacians and wall flux
-        float gmx = 0.f, gmy = 0.f, gpx = 0.f, gpy = 0.f, grx = 0.f, gry = 0.f;
-        float lapN_phi = 0.f, lapN_psi = 0.f, wf_phi = 0.f, wf_psi = 0.f;
-        const float drho = (P.rho_l - P.rho_g) * 0.5f * P.inv_phi_b;
+    // ------------------------------------------------------------------ stages
+    // staging: raw rows [r0, r0 + nrow) of (16 deviation planes, 2 moment planes, phi_prev)
+    // for window columns x0 - WOFF .. x0 - WOFF + WW - 1, into buffer b
+    auto issue = [&](int b, int r0, int nrow) {
+        unsigned char* base = sStg + (size_t)b * ST::BUF;
+        const int ws = x0 - WOFF;
+        if (vec) {
+            constexpr int CD = (int)(WW * sizeof(T) / 16);    // 16-byte chunks per deviation row
+            constexpr int CM = (int)(WW * sizeof(float2) / 16);
+            constexpr int CP = (int)(WW * sizeof(float) / 16);
+            constexpr int PER_ROW = 16 * CD + 2 * CM + CP;
+            const int items = nrow * PER_ROW;
+            for (int it = tid; it < items; it += NTHREADS) {
+                const int rr = it / PER_ROW;
+                int q = it - rr * PER_ROW;
+                const int y = r0 + rr;
+                if (y < 0 || y >= ny) continue;
+                unsigned char* row = base + (size_t)rr * ST::ROW;
+                const long long rowoff = (long long)y * nx + ws;
+                if (q < 16 * CD) {
+                    const int pl = q / CD, ch = q - pl * CD;
+                    const T* src = (pl < 8 ? A.gd_in : A.hd_in) + (long long)(pl & 7) * N + rowoff;
+                    cp_async16(row + (size_t)pl * WW * sizeof(T) + ch * 16, (const unsigned char*)src + ch * 16);
+                } else if ((q -= 16 * CD) < 2 * CM) {
+                    const int pl = q / CM, ch = q - pl * CM;
+                    cp_async16(row + ST::D_ROW + (size_t)pl * WW * sizeof(float2) + ch * 16,
+                               (const unsigned char*)((pl == 0 ? A.gm_in : A.hm_in) + rowoff) + ch * 16);
+                } else {
+                    q -= 2 * CM;
+                    cp_async16(row + ST::D_ROW + ST::M_ROW + q * 16, (const unsigned char*)(A.php_in + rowoff) + q * 16);
+                }
+            }
+            cp_async_commit();
+        } else {
+            // strips touching the periodic seam or unaligned grids: element-wise copy
+            const int items = nrow * WW;
+            for (int it = tid; it < items; it += NTHREADS) {
+                const int rr = it / WW, col = it - rr * WW;
+                const int y = r0 + rr;
+                if (y < 0 || y >= ny) continue;
+                unsigned char* row = base + (size_t)rr * ST::ROW;
+                const long long cidx = (long long)y * nx + wrapx(ws + col, nx);
+                T* dd = (T*)row;
 #pragma unroll
-        for (int k = 1; k < 9; ++k) {
-            const int cx = CXk(k), cy = CYk(k);
-            const int ny_ = gy + cy;
-            const bool out = (ny_ < 0 || ny_ >= ny);
-            const int oy = out ? 0 : cy;   // mirror: same row
-            const float mu = s_mu[l1y + oy][l1x + cx];
-            const float mp = s_mp[l1y + oy][l1x + cx];
-            const float vphi = s_ph[ly + oy][lx + cx];
-            const float vpsi = s_sh[ly + oy][lx + cx];
-            const float w3 = 3.0f * Wk(k);
-            gmx += w3 * cx * mu; gmy += w3 * cy * mu;
-            gpx += w3 * cx * mp; gpy += w3 * cy * mp;
-            grx += w3 * cx * vphi; gry += w3 * cy * vphi;
-            lapN_phi += Wk(k) * (vphi - phi);
-            lapN_psi += Wk(k) * (vpsi - psi);
-            if (out) {
-                const int w = ny_ < 0 ? 0 : 1;
-                wf_phi += Wk(k) * (s_gphi[w][lx + cx] - vphi);
-                wf_psi += Wk(k) * (s_gpsi[w][lx + cx] - vpsi);
+                for (int pl = 0; pl < 8; ++pl) {
+                    dd[pl * WW + col] = A.gd_in[(long long)pl * N + cidx];
+                    dd[(pl + 8) * WW + col] = A.hd_in[(long long)pl * N + cidx];
+                }
+                float2* mm = (float2*)(row + ST::D_ROW);
+                mm[col] = A.gm_in[cidx];
+                mm[WW + col] = A.hm_in[cidx];
+                ((float*)(row + ST::D_ROW + ST::M_ROW))[col] = A.php_in[cidx];
             }
         }
-        grx *= drho; gry *= drho;
-        lapN_phi *= 6.0f; lapN_psi *= 6.0f; wf_phi *= 6.0f; wf_psi *= 6.0f;
-        const float Fx = -phi * gmx - psi * gpx + P.Gx;
-        const float Fy = -phi * gmy - psi * gpy + P.Gy;
-        const float chi = 0.5f * (phi * P.inv_phi_b + 1.0f);
-        const float rho = P.rho_g + (P.rho_l - P.rho_g) * chi;
+    };
 
-        // flow pull with halfway bounce-back and the moving-wall term
+    // stage K from staging buffer b holding rows [r0, r0 + NROW)
+    auto stageK = [&](auto nrow_c, int b, int r0) {
+        constexpr int NROW = decltype(nrow_c)::value;
+        const unsigned char* base = sStg + (size_t)b * ST::BUF;
+        const int items = NROW * KX * nsets;
+        for (int it = tid; it < items; it += NTHREADS) {
+            const int kc = it % KX;
+            const int rest = it / KX;
+            const int rr = rest % NROW;
+            const int s = rest / NROW;
+            const int y = r0 + rr;
+            if (y < 0 || y >= ny) continue;
+            const int col = kc + (WOFF - 3);
+            const unsigned char* row = base + (size_t)rr * ST::ROW;
+            const float2 mv = ((const float2*)(row + ST::D_ROW))[s * WW + col];
+            ff mt = {mv.x, mv.y};
+            if (s == 0) {
+                if (qcoef != 0.0f) {
+                    const float php = ((const float*)(row + ST::D_ROW + ST::M_ROW))[col];
+                    mt = ff_add_f(mt, __fmul_rn(qcoef, hprime(php, P)));
+                }
+            } else {
+                mt = ff_add(mt, cuni);
+            }
+            const T* dd = (const T*)row + (size_t)(8 * s) * WW + col;
+            const float scl = s == 0 ? sc_phi : sc_psi;
+            // fixed point of v = d + w mh: K = rint(d * 2^S + (w 2^S) mh), evaluated once per value
+            const float ma = __fmul_rn(__fmul_rn(Wk(1), scl), mt.hi);
+            const float md = __fmul_rn(__fmul_rn(Wk(5), scl), mt.hi);
+            int ksum = 0;
+            int* kd = &KR(s, 1, y, kc);
+            static_for<1, 9>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                const int kv = __float2int_rn(__fmaf_rn(Stor<T>::lds(dd, (k - 1) * WW), scl, k < 5 ? ma : md));
+                kd[(k - 1) * RING * KX] = kv;
+                ksum += kv;
+            });
+            // m~ minus everything the node sends, so that phi = this + (everything it receives)
+            const ff basev = ff_add(mt, fixed_to_ff(-ksum, s == 0 ? isc_phi : isc_psi));
+            MT(s, y, kc) = make_float2(basev.hi, basev.lo);
+        }
+    };
+
+    auto stagePhi = [&](auto nrow_c, int r0) {
+        constexpr int nrow = decltype(nrow_c)::value;
+        const int items = nrow * PX * 2;
+        for (int it = tid; it < items; it += NTHREADS) {
+            const int pc = it % PX;
+            const int rest = it / PX;
+            const int rr = rest % nrow;
+            const int s = rest / nrow;
+            const int y = r0 + rr;
+            if (y < 0 || y >= ny) continue;
+            if (s == 1 && !P.psi_on) { SH(y, pc) = 0.0f; SL(y, pc) = 0.0f; continue; }
+            const int kc = pc + 1;
+            const float2 mv = MT(s, y, kc);
+            const ff mt = {mv.x, mv.y};
+            int ks = 0;
+            if (y > 0 && y < ny - 1) {
+                static_for<1, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    ks += KR(s, k, y - CYk(k), kc - CXk(k));
+                });
+            } else {
+                static_for<1, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    ks += k_in(sK, s, k, y, kc, ny);
+                });
+            }
+            const ff v = ff_add(mt, fixed_to_ff(ks, s == 0 ? isc_phi : isc_psi));
+            if (s == 0) { PH(y, pc) = v.hi; PL(y, pc) = v.lo; }
+            else { SH(y, pc) = v.hi; SL(y, pc) = v.lo; }
+        }
+    };
+
+    auto stageMu = [&](auto nrow_c, int r0) {
+        constexpr int nrow = decltype(nrow_c)::value;
+        const int items = nrow * MX;
+        for (int it = tid; it < items; it += NTHREADS) {
+            const int mc = it % MX;
+            const int y = r0 + it / MX;
+            if (y < 0 || y >= ny) continue;
+            const int pc = mc + 1;
+            const float phi = PH(y, pc), psi = SH(y, pc);
+            float lp = 0.0f, ls = 0.0f;
+            if (y > 0 && y < ny - 1) {
+                static_for<1, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    lp += Wk(k) * PH(y + CYk(k), pc + CXk(k));
+                    ls += Wk(k) * SH(y + CYk(k), pc + CXk(k));
+                });
+            } else {
+                // ghost row beyond the wall: Eq. boundary (reading c2), three columns
+                const int w = y == 0 ? 0 : 1;
+                const int side = y == 0 ? -1 : 1;
+                float gph[3], gps[3];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) wall_ghost(PH(y, pc - 1 + j), SH(y, pc - 1 + j), w, P, gph[j], gps[j]);
+                static_for<1, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    const bool out = (CYk(k) == side) || (y + CYk(k) < 0) || (y + CYk(k) >= ny);
+                    const float vphi = out ? gph[CXk(k) + 1] : PH(y + CYk(k), pc + CXk(k));
+                    const float vpsi = out ? gps[CXk(k) + 1] : SH(y + CYk(k), pc + CXk(k));
+                    lp += Wk(k) * vphi;
+                    ls += Wk(k) * vpsi;
+                });
+            }
+            const float lapG_phi = 6.0f * (lp - (1.0f - Wk(0)) * phi);
+            const float lapG_psi = 6.0f * (ls - (1.0f - Wk(0)) * psi);
+            MU(y, mc) = 4.0f * P.beta * (1.0f - psi) * (phi * phi * phi - phi) - P.kappa * lapG_phi + P.W * psi * phi;
+            if (P.psi_on) {
+                const float psc = fminf(fmaxf(psi, P.psi_clamp), 1.0f - P.psi_clamp);
+                const float om = 1.0f - phi * phi;
+                MP(y, mc) = P.kT * (__logf(psc) - __logf(1.0f - psc)) - P.lambda_s * lapG_psi - P.beta * om * om +
+                            0.5f * P.W * phi * phi;
+            } else {
+                MP(y, mc) = 0.0f;
+            }
+        }
+    };
+
+    auto stageCollide = [&](int r0, int r1) {
+        const int cc = tid % TX;
+        const int y = r0 + tid / TX;
+        const int gx = x0 + cc;
+        if (y >= r1 || gx >= nx) return;
+        const long long c = (long long)y * nx + gx;
+        const int pc = cc + 2, mc = cc + 1, kc = cc + 3;
+        const ff phff = {PH(y, pc), PL(y, pc)};
+        const ff psff = {SH(y, pc), SL(y, pc)};
+        const float phi = phff.hi, psi = psff.hi;
+        const bool wall_row = (y == 0 || y == ny - 1);
+
+        // flow pull first (longest latency): halfway bounce-back with the moving-wall term
         float f[9];
         const float php_self = __ldg(A.php_in + c);
-        const float rho_w = P.rho_g + (P.rho_l - P.rho_g) * 0.5f * (php_self * P.inv_phi_b + 1.0f);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int sy = gy - CYk(k);
-            if (sy < 0 || sy >= ny) {
-                const int o = OPPk(k);
-                const int w = sy < 0 ? 0 : 1;
-                f[k] = Stor<T>::ld(A.f_in, (long long)o * N + c) - 6.0f * Wk(o) * rho_w * CXk(o) * P.uw[w];
-            } else {
-                const int sx = wrapx(gx - CXk(k), nx);
-                f[k] = Stor<T>::ld(A.f_in, (long long)k * N + (long long)sy * nx + sx);
+        {
+            const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
+            const T* fin = A.f_in;
+            const long long rm = c - gx + (long long)(y > 0 ? -nx : 0);      // row y - 1 (clamped)
+            const long long r0c = c - gx;
+            const long long rp1 = c - gx + (long long)(y < ny - 1 ? nx : 0);  // row y + 1 (clamped)
+            static_for<0, 9>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                constexpr int cx = CXk(k), cy = CYk(k);
+                const int sx = cx == 0 ? gx : (cx > 0 ? xm : xp);
+                const long long rowb = cy == 0 ? r0c : (cy > 0 ? rm : rp1);
+                f[k] = Stor<T>::ld(fin, (long long)k * N + rowb + sx);
+            });
+            if (wall_row) {
+                const float rho_w = VARRHO ? P.rho_g + (P.rho_l - P.rho_g) * 0.5f * (php_self * P.inv_phi_b + 1.0f) : P.rho_l;
+                static_for<1, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    constexpr int o = OPPk(k);
+                    const int sy = y - CYk(k);
+                    if (sy < 0 || sy >= ny)
+                        f[k] = addc(Stor<T>::ld(fin, (long long)o * N + c), -CXk(o),
+                                    6.0f * Wk(o) * rho_w * P.uw[sy < 0 ? 0 : 1]);
+                });
             }
         }
-        float jx = 0.f, jy = 0.f, fsum = 0.f;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            jx += CXk(k) * f[k];
-            jy += CYk(k) * f[k];
-            if (k) fsum += f[k];
+
+        // gradients (mirror ghosts for mu and rho), Neumann Laplacian of psi, wall flux
+        float gmx = 0.f, gmy = 0.f, gpx = 0.f, gpy = 0.f, grx = 0.f, gry = 0.f;
+        float lns = 0.f, wf_phi = 0.f, wf_psi = 0.f;
+        if (!wall_row) {
+            static_for<1, 9>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                constexpr int cx = CXk(k), cy = CYk(k);
+                constexpr float w3 = 3.0f * Wk(k);
+                const float mu = w3 * MU(y + cy, mc + cx);
+                const float mp = w3 * MP(y + cy, mc + cx);
+                gmx = addc(gmx, cx, mu); gmy = addc(gmy, cy, mu);
+                gpx = addc(gpx, cx, mp); gpy = addc(gpy, cy, mp);
+                if (VARRHO) {
+                    const float vphi = w3 * PH(y + cy, pc + cx);
+                    grx = addc(grx, cx, vphi); gry = addc(gry, cy, vphi);
+                }
+                lns += Wk(k) * SH(y + cy, pc + cx);
+            });
+        } else {
+            const int w = y == 0 ? 0 : 1;
+            static_for<1, 9>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                constexpr int cx = CXk(k), cy = CYk(k);
+                constexpr float w3 = 3.0f * Wk(k);
+                const bool out = (y + cy < 0) || (y + cy >= ny);
+                const int ym = out ? y : y + cy;   // mirror: same row
+                const float mu = w3 * MU(ym, mc + cx);
+                const float mp = w3 * MP(ym, mc + cx);
+                gmx = addc(gmx, cx, mu); gmy = addc(gmy, cy, mu);
+                gpx = addc(gpx, cx, mp); gpy = addc(gpy, cy, mp);
+                const float vphi = PH(ym, pc + cx);
+                const float vpsi = SH(ym, pc + cx);
+                if (VARRHO) { grx = addc(grx, cx, w3 * vphi); gry = addc(gry, cy, w3 * vphi); }
+                lns += Wk(k) * vpsi;
+                if (out) {
+                    float gph, gps;
+                    wall_ghost(vphi, vpsi, w, P, gph, gps);
+                    wf_phi += Wk(k) * (gph - vphi);
+                    wf_psi += Wk(k) * (gps - vpsi);
+                }
+            });
         }
-        const float inv_rho = 1.0f / rho;
+        const float lapN_psi = 6.0f * (lns - (1.0f - Wk(0)) * psi);
+        wf_phi *= 6.0f; wf_psi *= 6.0f;
+        const float Fx = -phi * gmx - psi * gpx + P.Gx;
+        const float Fy = -phi * gmy - psi * gpy + P.Gy;
+        float chi = 0.f, rho = P.rho_l, inv_rho = inv_rho_l;
+        if (VARRHO) {
+            const float drho = (P.rho_l - P.rho_g) * 0.5f * P.inv_phi_b;
+            grx *= drho; gry *= drho;
+            chi = 0.5f * (phi * P.inv_phi_b + 1.0f);
+            rho = P.rho_g + (P.rho_l - P.rho_g) * chi;
+            inv_rho = __frcp_rn(rho);
+        }
+
+        float jx = 0.f, jy = 0.f, fsum = 0.f;
+        static_for<0, 9>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            jx = addc(jx, CXk(k), f[k]);
+            jy = addc(jy, CYk(k), f[k]);
+            if (k) fsum += f[k];
+        });
         const float ux = (jx + 0.5f * Fx) * inv_rho;
         const float uy = (jy + 0.5f * Fy) * inv_rho;
         const float usq = ux * ux + uy * uy;
-        const float ugr = ux * grx + uy * gry;
+        const float ugr = VARRHO ? ux * grx + uy * gry : 0.0f;
         const float pres = (1.0f / 3.0f) / (1.0f - Wk(0)) * (fsum + 0.5f * ugr - rho * Wk(0) * usq * 1.5f);
 
         const float hp = hprime(phi, P);
-        float mu_self = s_mu[l1y][l1x];
         if (P.psi_on) clamps += (psi < P.psi_clamp || psi > 1.0f - P.psi_clamp) ? 1.0f : 0.0f;
-
-        // accumulate the global integrals at this time level
-        acc[P_S1] = ff_add_f(acc[P_S1], hp * mu_self);
-        acc[P_S2] = ff_add_f(acc[P_S2], hp * hp);
+        s1acc += hp * MU(y, mc);
+        s2acc += hp * hp;
+        kinacc += 0.5f * rho * usq;
         {
             const float u = phi * P.inv_phi_b;
             acc[P_Q] = ff_add_f(acc[P_Q], 1.5f * u - 0.5f * u * u * u);
         }
         acc[P_PHI] = ff_add(acc[P_PHI], phff);
         acc[P_PSI] = ff_add(acc[P_PSI], psff);
-        acc[P_KIN] = ff_add_f(acc[P_KIN], 0.5f * rho * usq);
         range |= !(fabsf(ux) < 1.0f && fabsf(uy) < 1.0f && fabsf(phi) < 2.0f && fabsf(pres) < 1e3f);
+
+        // free reaction term of the surfactant (R_psi without mubar), rounded to storage
+        float Rf_psi = 0.0f;
+        if (P.psi_on) {
+            const float psc = fminf(fmaxf(psi, P.psi_clamp), 1.0f - P.psi_clamp);
+            const float om = 1.0f - phi * phi;
+            Rf_psi = Stor<T>::rnd(P.M_psi * (-P.kT * (__logf(psc) - __logf(1.0f - psc)) + P.beta * om * om -
+                                             0.5f * P.W * phi * phi + P.lambda_s * wf_psi) - P.M_0 * lapN_psi);
+            acc[P_S3] = ff_add_f(acc[P_S3], Rf_psi);
+        }
 
         if (DIAG) {
             if (A.o_phi) {
@@ -411,192 +621,215 @@ __global__ void __launch_bounds__(NTHREADS) step_kernel(const StepArgs<T> A) {
                 A.o_uy[c] = (double)uy;
                 A.o_p[c] = (double)pres;
             }
-            // S3 of the diagnostic level: the free reaction term as the next step would form it
-            if (P.psi_on) {
-                float psc = fminf(fmaxf(psi, P.psi_clamp), 1.0f - P.psi_clamp);
-                float om = 1.0f - phi * phi;
-                float Rf = P.M_psi * (-P.kT * logf(psc / (1.0f - psc)) + P.beta * om * om - 0.5f * P.W * phi * phi +
-                                      P.lambda_s * wf_psi) - P.M_0 * lapN_psi;
-                acc[P_S3] = ff_add_f(acc[P_S3], Stor<T>::rnd(Rf));
-            }
-            continue;
+            return;
         }
 
         // ---- flow collision (Sec. 3): f^eq, source F_{i,1}
         {
-            float feq[9], src[9];
-            const float p3 = 3.0f * pres;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const float cu = CXk(k) * ux + CYk(k) * uy;
-                const float cF = CXk(k) * Fx + CYk(k) * Fy;
-                const float cg = CXk(k) * grx + CYk(k) * gry;
-                feq[k] = p3 * (Wk(k) - (k == 0 ? 1.0f : 0.0f)) + rho * Wk(k) * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq);
-                src[k] = Wk(k) * (ugr + 3.0f * cF + 3.0f * (cu * cg - (1.0f / 3.0f) * ugr));
-            }
             float s2 = P.sf[2];
-            if (P.var_nu) {
+            if (VARRHO) {
                 const float nu = P.nu_g + (P.nu_l - P.nu_g) * chi;
-                s2 = 1.0f / (3.0f * nu + 0.5f);
+                s2 = __frcp_rn(3.0f * nu + 0.5f);
             }
+            const float p3 = 3.0f * pres - 1.5f * rho * usq;
+            T* fo = A.f_out + c;
             if (P.mrt_f) {
-                float s[9];
-                s[0] = P.sf[0] > 0.f ? P.sf[0] : s2;
-                s[1] = s[2] = P.sf[1] > 0.f ? P.sf[1] : s2;
-                s[3] = s[4] = s[5] = s2;
-                s[6] = s[7] = P.sf[3] > 0.f ? P.sf[3] : s2;
-                s[8] = P.sf[4] > 0.f ? P.sf[4] : s2;
-                mrt_collide(f, feq, src, s);
+                float feq[9], src[9], sv[9];
+                static_for<0, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    const float cu = cdot(k, ux, uy);
+                    feq[k] = Wk(k) * (p3 + rho * (3.0f * cu + 4.5f * cu * cu)) - (k == 0 ? 3.0f * pres : 0.0f);
+                    float sk = 3.0f * cdot(k, Fx, Fy);
+                    if (VARRHO) sk += ugr + 3.0f * (cu * cdot(k, grx, gry) - (1.0f / 3.0f) * ugr);
+                    src[k] = Wk(k) * sk;
+                });
+                sv[0] = P.sf[0] > 0.f ? P.sf[0] : s2;
+                sv[1] = sv[2] = P.sf[1] > 0.f ? P.sf[1] : s2;
+                sv[3] = sv[4] = sv[5] = s2;
+                sv[6] = sv[7] = P.sf[3] > 0.f ? P.sf[3] : s2;
+                sv[8] = P.sf[4] > 0.f ? P.sf[4] : s2;
+                mrt_collide(f, feq, src, sv);
+                static_for<0, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    Stor<T>::st(fo, (long long)k * N, f[k]);
+                });
             } else {
                 const float a = 1.0f - 0.5f * s2;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) f[k] = f[k] - s2 * (f[k] - feq[k]) + a * src[k];
+                static_for<0, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    const float cu = cdot(k, ux, uy);
+                    const float feq = Wk(k) * (p3 + rho * (3.0f * cu + 4.5f * cu * cu)) - (k == 0 ? 3.0f * pres : 0.0f);
+                    float sk = 3.0f * cdot(k, Fx, Fy);
+                    if (VARRHO) sk += ugr + 3.0f * (cu * cdot(k, grx, gry) - (1.0f / 3.0f) * ugr);
+                    Stor<T>::st(fo, (long long)k * N, f[k] + s2 * (feq - f[k]) + a * Wk(k) * sk);
+                });
             }
-#pragma unroll
-            for (int k = 0; k < 9; ++k) Stor<T>::st(A.f_out, (long long)k * N + c, f[k]);
         }
 
         // ---- history of the source terms (Sec. 3, backward differences)
         const float phux = phi * ux, phuy = phi * uy, psux = psi * ux, psuy = psi * uy;
         float dphux = 0.f, dphuy = 0.f, dpsux = 0.f, dpsuy = 0.f, Rp_phi = 0.f, Rp_psi = 0.f;
+        T* hi_ = A.hist + c;
         if (!A.first) {
-            Rp_phi = Stor<T>::ld(A.hist, 0 * N + c);
-            Rp_psi = Stor<T>::ld(A.hist, 1 * N + c);
-            dphux = phux - Stor<T>::ld(A.hist, 2 * N + c);
-            dphuy = phuy - Stor<T>::ld(A.hist, 3 * N + c);
-            dpsux = psux - Stor<T>::ld(A.hist, 4 * N + c);
-            dpsuy = psuy - Stor<T>::ld(A.hist, 5 * N + c);
+            Rp_phi = Stor<T>::ld(hi_, 0);
+            dphux = phux - Stor<T>::ld(hi_, 2 * N);
+            dphuy = phuy - Stor<T>::ld(hi_, 3 * N);
+            if (P.psi_on) {
+                Rp_psi = Stor<T>::ld(hi_, N);
+                dpsux = psux - Stor<T>::ld(hi_, 4 * N);
+                dpsuy = psuy - Stor<T>::ld(hi_, 5 * N);
+            }
         }
 
-        // ---- phase-field set
-        {
-            // R_phi without the lambda^n term (deferred), with the wall flux of reading c2
-            const float Rf = Stor<T>::rnd(P.M_phi * (-4.0f * P.beta * (1.0f - psi) * (phi * phi * phi - phi) -
-                                                     P.W * psi * phi + P.kappa * wf_phi));
-            // dR = R + (R - R_prev)/2, exact in float-float; minus the lambda^{n-1} part of R_prev
+        // ---- the two scalar sets share one code path
+#pragma unroll 1
+        for (int s = 0; s < nsets; ++s) {
+            const float cval = s == 0 ? phi : psi;
+            const ff cff = s == 0 ? phff : psff;
+            float Rf;
             ff dR;
+            if (s == 0) {
+                // R_phi without the lambda^n term (deferred), with the wall flux of reading c2
+                Rf = Stor<T>::rnd(P.M_phi * (-4.0f * P.beta * (1.0f - psi) * (phi * phi * phi - phi) -
+                                             P.W * psi * phi + P.kappa * wf_phi));
+            } else {
+                Rf = Rf_psi;
+            }
+            // dR = R + (R - R_prev)/2 exact in float-float, minus the multiplier part of R_prev
             if (A.first) {
                 dR = {Rf, 0.0f};
             } else {
-                ff t = two_sum(Rf, -Rp_phi);
+                const ff t = two_sum(Rf, s == 0 ? -Rp_phi : -Rp_psi);
                 dR = ff_add_f(ff_scale_pow2(t, 0.5f), Rf);
-                const float lam_part = (float)(0.5 * P.M_phi_d * rp.lam) * hprime(php_self, P);
-                dR = ff_add_f(dR, -lam_part);
+                if (s == 0) dR = ff_add_f(dR, -lam_half * hprime(php_self, P));
+                else dR = ff_add(dR, mub_half);
             }
-            const float dRf = dR.hi + dR.lo;
-            int Kin[9];
-            int rdummy = 0;
-            (void)pull_scalar<T, true>(A.gd_in, A.gm_in, A.php_in, gx, gy, nx, ny, N, qcoef, cuni, P, Kin, rdummy);
-            const float inv_scale = 1.0f / (float)(1u << SFIX_PHI);
+            const ff mstar = ff_add(cff, dR);
+            const float isc = s == 0 ? isc_phi : isc_psi;
             float g[9];
             float gs = 0.f;
-#pragma unroll
-            for (int k = 1; k < 9; ++k) { g[k] = (float)Kin[k] * inv_scale; gs += g[k]; }
-            g[0] = phi - gs;
-            float geq[9], src[9];
-            const float a3x = 3.0f * dphux, a3y = 3.0f * dphuy;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                geq[k] = Wk(k) * P.eta_phi * phi + (k == 0 ? (1.0f - P.eta_phi) * phi : 0.0f) +
-                         Wk(k) * 3.0f * (CXk(k) * phux + CYk(k) * phuy);
-                src[k] = Wk(k) * (CXk(k) * a3x + CYk(k) * a3y);
-            }
-            if (P.mrt_g) {
-                float s[9];
-                const float s1 = P.sg[1];
-                s[0] = P.sg[0] > 0.f ? P.sg[0] : s1;
-                s[1] = s[2] = s1;
-                s[3] = s[4] = s[5] = P.sg[2] > 0.f ? P.sg[2] : s1;
-                s[6] = s[7] = P.sg[3] > 0.f ? P.sg[3] : s1;
-                s[8] = P.sg[4] > 0.f ? P.sg[4] : s1;
-                mrt_collide(g, geq, src, s);
+            if (wall_row) {
+                static_for<1, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    g[k] = (float)k_in(sK, s, k, y, kc, ny) * isc;
+                    gs += g[k];
+                });
             } else {
-                const float s1 = P.sg[1], a = 1.0f - 0.5f * s1;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) g[k] = g[k] - s1 * (g[k] - geq[k]) + a * src[k];
+                static_for<1, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    g[k] = (float)KR(s, k, y - CYk(k), kc - CXk(k)) * isc;
+                    gs += g[k];
+                });
             }
-            const ff mstar = ff_add(phff, dR);
+            g[0] = cval - gs;
+            const float eta = s == 0 ? P.eta_phi : P.eta_psi;
+            const float ax = 3.0f * (s == 0 ? dphux : dpsux), ay = 3.0f * (s == 0 ? dphuy : dpsuy);
+            const float cux = 3.0f * (s == 0 ? phux : psux), cuy = 3.0f * (s == 0 ? phuy : psuy);
+            const float* sr = s == 0 ? P.sg : P.sh;
+            const int mrt = s == 0 ? P.mrt_g : P.mrt_h;
+            const float s1 = sr[1];
+            // the zeroth moment is carried exactly by m*; the deviations are g*_k - w_k hi(m*)
+            // with the local source w_k dR folded in:  g*_k + w_k (dR - hi(m*))
+            const float shift = (dR.hi + dR.lo) - mstar.hi;
+            T* dout = (s == 0 ? A.gd_out : A.hd_out) + c;
+            if (mrt) {
+                float geq[9], src[9], sv[9];
+                static_for<0, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    geq[k] = Wk(k) * (eta * cval + cdot(k, cux, cuy)) + (k == 0 ? (1.0f - eta) * cval : 0.0f);
+                    src[k] = Wk(k) * cdot(k, ax, ay);
+                });
+                sv[0] = sr[0] > 0.f ? sr[0] : s1;
+                sv[1] = sv[2] = s1;
+                sv[3] = sv[4] = sv[5] = sr[2] > 0.f ? sr[2] : s1;
+                sv[6] = sv[7] = sr[3] > 0.f ? sr[3] : s1;
+                sv[8] = sr[4] > 0.f ? sr[4] : s1;
+                mrt_collide(g, geq, src, sv);
+                static_for<1, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    Stor<T>::st(dout, (long long)(k - 1) * N, g[k] + Wk(k) * shift);
+                });
+            } else {
+                const float a = 1.0f - 0.5f * s1;
+                const float ec = eta * cval;
+                static_for<1, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    const float geq = Wk(k) * (ec + cdot(k, cux, cuy));
+                    const float gk = g[k] + s1 * (geq - g[k]) + a * Wk(k) * cdot(k, ax, ay);
+                    Stor<T>::st(dout, (long long)(k - 1) * N, gk + Wk(k) * shift);
+                });
+            }
             float2 mo;
             mo.x = mstar.hi;
             mo.y = mstar.lo;
-            A.gm_out[c] = mo;
-#pragma unroll
-            for (int k = 1; k < 9; ++k)
-                Stor<T>::st(A.gd_out, (long long)(k - 1) * N + c, g[k] + Wk(k) * dRf - Wk(k) * mstar.hi);
-            A.php_out[c] = phi;
-            Stor<T>::st(A.hist, 0 * N + c, Rf);
-            Stor<T>::st(A.hist, 2 * N + c, phux);
-            Stor<T>::st(A.hist, 3 * N + c, phuy);
+            (s == 0 ? A.gm_out : A.hm_out)[c] = mo;
+            Stor<T>::st(hi_, (long long)s * N, Rf);
+            Stor<T>::st(hi_, (long long)(2 + 2 * s) * N, s == 0 ? phux : psux);
+            Stor<T>::st(hi_, (long long)(3 + 2 * s) * N, s == 0 ? phuy : psuy);
         }
+        A.php_out[c] = phi;
+    };
 
-        // ---- surfactant set
-        if (P.psi_on) {
-            const float psc = fminf(fmaxf(psi, P.psi_clamp), 1.0f - P.psi_clamp);
-            const float om = 1.0f - phi * phi;
-            const float Rf = Stor<T>::rnd(P.M_psi * (-P.kT * logf(psc / (1.0f - psc)) + P.beta * om * om -
-                                                     0.5f * P.W * phi * phi + P.lambda_s * wf_psi) -
-                                          P.M_0 * lapN_psi);
-            acc[P_S3] = ff_add_f(acc[P_S3], Rf);
-            ff dR;
-            if (A.first) {
-                dR = {Rf, 0.0f};
-            } else {
-                ff t = two_sum(Rf, -Rp_psi);
-                dR = ff_add_f(ff_scale_pow2(t, 0.5f), Rf);
-                const double hm = -0.5 * rp.mpsi_mubar;
-                ff hmf;
-                hmf.hi = (float)hm;
-                hmf.lo = (float)(hm - (double)hmf.hi);
-                dR = ff_add(dR, hmf);
-            }
-            const float dRf = dR.hi + dR.lo;
-            int Kin[9];
-            int rdummy = 0;
-            (void)pull_scalar<T, false>(A.hd_in, A.hm_in, A.php_in, gx, gy, nx, ny, N, 0.0f, cuni, P, Kin, rdummy);
-            const float inv_scale = 1.0f / 2147483648.0f;
-            float h[9];
-            float hs = 0.f;
-#pragma unroll
-            for (int k = 1; k < 9; ++k) { h[k] = (float)Kin[k] * inv_scale; hs += h[k]; }
-            h[0] = psi - hs;
-            float heq[9], src[9];
-            const float a3x = 3.0f * dpsux, a3y = 3.0f * dpsuy;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                heq[k] = Wk(k) * P.eta_psi * psi + (k == 0 ? (1.0f - P.eta_psi) * psi : 0.0f) +
-                         Wk(k) * 3.0f * (CXk(k) * psux + CYk(k) * psuy);
-                src[k] = Wk(k) * (CXk(k) * a3x + CYk(k) * a3y);
-            }
-            if (P.mrt_h) {
-                float s[9];
-                const float s1 = P.sh[1];
-                s[0] = P.sh[0] > 0.f ? P.sh[0] : s1;
-                s[1] = s[2] = s1;
-                s[3] = s[4] = s[5] = P.sh[2] > 0.f ? P.sh[2] : s1;
-                s[6] = s[7] = P.sh[3] > 0.f ? P.sh[3] : s1;
-                s[8] = P.sh[4] > 0.f ? P.sh[4] : s1;
-                mrt_collide(h, heq, src, s);
-            } else {
-                const float s1 = P.sh[1], a = 1.0f - 0.5f * s1;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) h[k] = h[k] - s1 * (h[k] - heq[k]) + a * src[k];
-            }
-            const ff mstar = ff_add(psff, dR);
-            float2 mo;
-            mo.x = mstar.hi;
-            mo.y = mstar.lo;
-            A.hm_out[c] = mo;
-#pragma unroll
-            for (int k = 1; k < 9; ++k)
-                Stor<T>::st(A.hd_out, (long long)(k - 1) * N + c, h[k] + Wk(k) * dRf - Wk(k) * mstar.hi);
-            Stor<T>::st(A.hist, 1 * N + c, Rf);
-            Stor<T>::st(A.hist, 4 * N + c, psux);
-            Stor<T>::st(A.hist, 5 * N + c, psuy);
+    // --------------------------------------------------------------- pipeline
+    using I2 = std::integral_constant<int, 2>;
+    using I4 = std::integral_constant<int, 4>;
+    const long long total = A.total;
+    long long lo = total * blockIdx.x / gridDim.x;
+    const long long hi = total * (blockIdx.x + 1) / gridDim.x;
+    while (lo < hi) {
+        const int strip = (int)(lo / ny);
+        ys = (int)(lo - (long long)strip * ny);
+        ye = (int)min((long long)ny, (long long)ys + (hi - lo));
+        lo += ye - ys;
+        x0 = strip * TX;
+        vec = (x0 - WOFF >= 0) && (x0 - WOFF + WW <= nx) && (nx % VEC == 0);
+        __syncthreads();   // the previous piece's last collide read the rings
+        issue(0, ys - 3, 4);
+        cp_async_wait_all();
+        __syncthreads();
+        stageK(I4{}, 0, ys - 3);
+        __syncthreads();
+        issue(0, ys + 1, 2);
+        cp_async_wait_all();
+        __syncthreads();
+        stageK(I2{}, 0, ys + 1);
+        __syncthreads();
+        issue(1, ys + 3, RB);
+        stagePhi(I4{}, ys - 2);
+        __syncthreads();
+        stageMu(I2{}, ys - 1);
+        __syncthreads();
+        int b = 1;
+        for (int r = ys; r < ye; r += RB) {
+            cp_async_wait_all();
+            __syncthreads();
+            if (r + RB < ye) issue(b ^ 1, r + RB + 3, RB);   // next iteration's rows, overlapped
+            stageK(I4{}, b, r + 3);
+            __syncthreads();
+            stagePhi(I4{}, r + 2);
+            __syncthreads();
+            stageMu(I4{}, r + 1);
+            __syncthreads();
+            stageCollide(r, min(r + RB, ye));
+            __syncthreads();
+            b ^= 1;
         }
     }
     acc[P_CLAMP] = {clamps, 0.0f};
     acc[P_RANGE] = {(float)range, 0.0f};
+    acc[P_S1] = {s1acc, 0.0f};
+    acc[P_S2] = {s2acc, 0.0f};
+    acc[P_KIN] = {kinacc, 0.0f};
     finish_reduction<T>(acc, A, DIAG);
 }
+
+#undef KR
+#undef MT
+#undef PH
+#undef PL
+#undef SH
+#undef SL
+#undef MU
+#undef MP
 
 }  // namespace slbm
