@@ -147,6 +147,40 @@ slbm_status slbm_read_fields(slbm_domain* d, double* phi, double* psi,
  * Returns EUNSTABLE (with *t filled) when range_count > 0 or a total is non-finite. */
 slbm_status slbm_read_totals(slbm_domain* d, slbm_totals* t);
 
+/* Fields and totals at the current time level, written into device memory the
+ * caller owns, without allocating anything.  (The paper has no counterpart: this is
+ * an interface for callers, not part of the method.)
+ *
+ * For callers that cannot call cudaMalloc once they are running: host frameworks or
+ * memory pools that own and budget all device memory and forbid allocation after
+ * set-up, and loops where the device-wide synchronisation an allocation or free can
+ * imply would stall other streams.  slbm_read_fields allocates a 5 * nx * ny double
+ * buffer on its first call; this variant writes straight into the caller's buffers.
+ *
+ * phi, psi, ux, uy, p: DEVICE pointers (this domain's device), nx*ny doubles each,
+ * row-major [ny][nx]; any may be NULL (then that field is not written).  totals: host
+ * pointer or NULL.  With totals != NULL the call synchronises the domain's stream and
+ * fills *totals (same meaning and status rules as slbm_read_totals); with NULL it only
+ * queues the work on the stream.
+ *
+ * Scratch: the per-CTA partial sums, the completion counter and the result record live
+ * in one file-scope static device array of SLBM_NOALLOC_SCRATCH_BYTES (about 74 KB),
+ * held by every GPU that loads this library until the process exits.  The array holds
+ * at most SLBM_NOALLOC_MAX_CTAS CTAs of partials; a domain whose grid is larger is
+ * rejected with SLBM_EINVAL (grids here are at most 2 CTAs per SM).  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current, so that first call should come before any stream capture.  Every call on a
+ * device shares the one array and it keeps the last call's contents (the counter is
+ * cleared at the start of each call): calls that overlap on the GPU, from any domain
+ * or stream, race and must be serialised by the caller.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ * Errors: EINVAL (NULL domain, grid too large), ESTATE (fields never initialised),
+ * ECUDA, EUNSTABLE (as slbm_read_totals). */
+#define SLBM_NOALLOC_MAX_CTAS 1024
+#define SLBM_NOALLOC_SCRATCH_BYTES (SLBM_NOALLOC_MAX_CTAS * 9 * 8 + 256 + 128)
+slbm_status slbm_read_fields_noalloc(slbm_domain* d, double* phi, double* psi, double* ux, double* uy,
+                                     double* p, slbm_totals* totals);
+
 /* Bytes of device memory the domain holds. */
 size_t slbm_device_bytes(const slbm_domain* d);
 

@@ -64,6 +64,8 @@ def _load():
     L.slbm_step.argtypes = [vp, ll]
     L.slbm_read_fields.argtypes = [vp, dp, dp, dp, dp, dp]
     L.slbm_read_totals.argtypes = [vp, ctypes.POINTER(Totals)]
+    L.slbm_read_fields_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(Totals)]
+    L.slbm_read_fields_noalloc.restype = ctypes.c_int
     L.slbm_device_bytes.argtypes = [vp]
     L.slbm_device_bytes.restype = ctypes.c_size_t
     L.slbm_destroy.argtypes = [vp]
@@ -153,6 +155,23 @@ class Domain:
         if check:
             self._check(st)
         return {name: getattr(t, name) for name, _ in Totals._fields_}
+
+    def read_fields_noalloc(self, phi=None, psi=None, ux=None, uy=None, p=None, totals=True):
+        """Fields written into caller-owned DEVICE buffers (e.g. torch CUDA tensors of
+        float64 with nx*ny elements, or raw device addresses); the library allocates
+        nothing.  Returns the totals dict when ``totals`` is true (synchronises)."""
+        def ptr(x):
+            if x is None:
+                return None
+            if hasattr(x, "data_ptr"):
+                if x.numel() != self.nx * self.ny or x.element_size() != 8 or not x.is_contiguous():
+                    raise ValueError("device buffers must be contiguous float64 with nx*ny elements")
+                return ctypes.c_void_p(x.data_ptr())
+            return ctypes.c_void_p(int(x))
+        t = Totals() if totals else None
+        self._check(lib.slbm_read_fields_noalloc(self._h, ptr(phi), ptr(psi), ptr(ux), ptr(uy), ptr(p),
+                                                 ctypes.byref(t) if t is not None else None))
+        return {name: getattr(t, name) for name, _ in Totals._fields_} if t is not None else None
 
     @property
     def device_bytes(self):

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -303,6 +304,60 @@ slbm_status dalloc(slbm_domain* d, P** ptr, size_t bytes) {
     return SLBM_OK;
 }
 
+// ---- scratch of slbm_read_fields_noalloc: static device memory, no allocation
+static_assert(sizeof(Rec) <= 128, "record must fit the scratch tail");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SLBM_NOALLOC_SCRATCH_BYTES];
+
+// device address of g_noalloc_scratch, looked up once per device with that device current
+cudaError_t noalloc_scratch(unsigned char** out) {
+    static std::mutex mtx;
+    static unsigned char* addr[128] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mtx);
+    if (!addr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = (unsigned char*)ptr;
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t launch_diag_noalloc(slbm_domain* d, unsigned char* scratch, double* o[5]) {
+    cudaError_t e = prepare_kernels<T>();
+    if (e != cudaSuccess) return e;
+    StepArgs<T> a = make_args<T>(d, true);
+    a.partials = (double*)scratch;
+    a.counter = (unsigned int*)(scratch + SLBM_NOALLOC_MAX_CTAS * 9 * 8);
+    a.rec_out = (Rec*)(scratch + SLBM_NOALLOC_MAX_CTAS * 9 * 8 + 256);
+    a.o_phi = o[0]; a.o_psi = o[1]; a.o_ux = o[2]; a.o_uy = o[3]; a.o_p = o[4];
+    const bool var = a.P.var_nu || a.P.rho_l != a.P.rho_g;
+    const size_t sm = smem_bytes<T>();
+    if (var) step_kernel<T, true, true><<<d->grid, NTHREADS, sm, d->stream>>>(a);
+    else step_kernel<T, true, false><<<d->grid, NTHREADS, sm, d->stream>>>(a);
+    return cudaGetLastError();
+}
+
+void fill_totals(const slbm_domain* d, const Rec& r, slbm_totals* t) {
+    t->step = d->n;
+    t->Q_phi = r.Q;
+    t->H = r.H;
+    t->phi_total = r.phi_tot;
+    t->psi_total = r.psi_tot;
+    t->lambda_phi = r.lam;
+    t->mubar_psi = (d->p.psi_on && d->p.M_psi > 0) ? r.mpsi_mubar / d->p.M_psi : 0.0;
+    t->kinetic = r.kin;
+    t->S1 = r.S1;
+    t->S2 = r.S2;
+    t->clamp_count = (long long)r.clamps;
+    t->range_count = (long long)r.range;
+}
+
 }  // namespace
 
 extern "C" {
@@ -457,18 +512,40 @@ slbm_status slbm_read_totals(slbm_domain* d, slbm_totals* t) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, d->recs + 2, sizeof(Rec), cudaMemcpyDeviceToHost, d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) return cuda_fail(d, e, "read_totals");
-    t->step = d->n;
-    t->Q_phi = r.Q;
-    t->H = r.H;
-    t->phi_total = r.phi_tot;
-    t->psi_total = r.psi_tot;
-    t->lambda_phi = r.lam;
-    t->mubar_psi = (d->p.psi_on && d->p.M_psi > 0) ? r.mpsi_mubar / d->p.M_psi : 0.0;
-    t->kinetic = r.kin;
-    t->S1 = r.S1;
-    t->S2 = r.S2;
-    t->clamp_count = (long long)r.clamps;
-    t->range_count = (long long)r.range;
+    fill_totals(d, r, t);
+    const bool finite = std::isfinite(r.Q) && std::isfinite(r.psi_tot) && std::isfinite(r.lam) && std::isfinite(r.kin);
+    if (t->range_count > 0 || !finite) return fail(d, SLBM_EUNSTABLE, "the run has diverged (non-finite or out-of-range values)");
+    return SLBM_OK;
+}
+
+slbm_status slbm_read_fields_noalloc(slbm_domain* d, double* phi, double* psi, double* ux, double* uy,
+                                     double* p, slbm_totals* t) {
+    if (!d) return SLBM_EINVAL;
+    if (!d->initialised) return fail(d, SLBM_ESTATE, "fields not initialised");
+    if (d->grid.x * d->grid.y > SLBM_NOALLOC_MAX_CTAS)
+        return fail(d, SLBM_EINVAL, "grid larger than the static scratch of slbm_read_fields_noalloc (" +
+                                        std::to_string(SLBM_NOALLOC_MAX_CTAS) + " CTAs)");
+    unsigned char* scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return cuda_fail(d, e, "cudaGetSymbolAddress (noalloc scratch)");
+    // the completion counter must start at zero
+    e = cudaMemsetAsync(scratch + SLBM_NOALLOC_MAX_CTAS * 9 * 8, 0, sizeof(unsigned int), d->stream);
+    double* o[5] = {phi, psi, ux, uy, p};
+    if (e == cudaSuccess) {
+        switch (d->p.precision) {
+            case SLBM_FP16DEV: e = launch_diag_noalloc<__half>(d, scratch, o); break;
+            case SLBM_BF16DEV: e = launch_diag_noalloc<__nv_bfloat16>(d, scratch, o); break;
+            default: e = launch_diag_noalloc<float>(d, scratch, o); break;
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(d, e, "read_fields_noalloc");
+    if (!t) return SLBM_OK;
+    Rec r;
+    e = cudaMemcpyAsync(&r, scratch + SLBM_NOALLOC_MAX_CTAS * 9 * 8 + 256, sizeof(Rec), cudaMemcpyDeviceToHost,
+                        d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    if (e != cudaSuccess) return cuda_fail(d, e, "read_fields_noalloc");
+    fill_totals(d, r, t);
     const bool finite = std::isfinite(r.Q) && std::isfinite(r.psi_tot) && std::isfinite(r.lam) && std::isfinite(r.kin);
     if (t->range_count > 0 || !finite) return fail(d, SLBM_EUNSTABLE, "the run has diverged (non-finite or out-of-range values)");
     return SLBM_OK;

@@ -614,13 +614,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
         }
 
         if (DIAG) {
-            if (A.o_phi) {
-                A.o_phi[c] = ff_to_d(phff);
-                A.o_psi[c] = ff_to_d(psff);
-                A.o_ux[c] = (double)ux;
-                A.o_uy[c] = (double)uy;
-                A.o_p[c] = (double)pres;
-            }
+            // each output may be absent on its own
+            if (A.o_phi) A.o_phi[c] = ff_to_d(phff);
+            if (A.o_psi) A.o_psi[c] = ff_to_d(psff);
+            if (A.o_ux) A.o_ux[c] = (double)ux;
+            if (A.o_uy) A.o_uy[c] = (double)uy;
+            if (A.o_p) A.o_p[c] = (double)pres;
             return;
         }
 
