@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
                 constexpr int cx = CXk(k), cy = CYk(k);
                 const int sx = cx == 0 ? gx : (cx > 0 ? xm : xp);
                 const long long rowb = cy == 0 ? r0c : (cy > 0 ? rm : rp1);
-                f[k] = Stor<T>::ld(fin, (long long)k * N + rowb + sx);
+                f[k] = Stor<T>::ld(fin + (k * (unsigned)N), rowb + sx);
             });
             if (wall_row) {
                 const float rho_w = VARRHO ? P.rho_g + (P.rho_l - P.rho_g) * 0.5f * (php_self * P.inv_phi_b + 1.0f) : P.rho_l;
@@ -590,18 +590,22 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
         const float ugr = VARRHO ? ux * grx + uy * gry : 0.0f;
         const float pres = (1.0f / 3.0f) / (1.0f - Wk(0)) * (fsum + 0.5f * ugr - rho * Wk(0) * usq * 1.5f);
 
+        // integrals the multipliers need (Eq. eq15, Eq. AC_psi); the diagnostic pass also
+        // reduces the reported totals and checks for divergence
         const float hp = hprime(phi, P);
-        if (P.psi_on) clamps += (psi < P.psi_clamp || psi > 1.0f - P.psi_clamp) ? 1.0f : 0.0f;
         s1acc += hp * MU(y, mc);
         s2acc += hp * hp;
-        kinacc += 0.5f * rho * usq;
-        {
+        if (DIAG || (P.target && !P.linear)) {
             const float u = phi * P.inv_phi_b;
             acc[P_Q] = ff_add_f(acc[P_Q], 1.5f * u - 0.5f * u * u * u);
         }
-        acc[P_PHI] = ff_add(acc[P_PHI], phff);
-        acc[P_PSI] = ff_add(acc[P_PSI], psff);
-        range |= !(fabsf(ux) < 1.0f && fabsf(uy) < 1.0f && fabsf(phi) < 2.0f && fabsf(pres) < 1e3f);
+        if (DIAG || (P.target && P.linear)) acc[P_PHI] = ff_add(acc[P_PHI], phff);
+        if (DIAG) {
+            if (P.psi_on) clamps += (psi < P.psi_clamp || psi > 1.0f - P.psi_clamp) ? 1.0f : 0.0f;
+            kinacc += 0.5f * rho * usq;
+            acc[P_PSI] = ff_add(acc[P_PSI], psff);
+            range |= !(fabsf(ux) < 1.0f && fabsf(uy) < 1.0f && fabsf(phi) < 2.0f && fabsf(pres) < 1e3f);
+        }
 
         // free reaction term of the surfactant (R_psi without mubar), rounded to storage
         float Rf_psi = 0.0f;
@@ -632,6 +636,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
             }
             const float p3 = 3.0f * pres - 1.5f * rho * usq;
             T* fo = A.f_out + c;
+            const unsigned Nu = (unsigned)N;
             if (P.mrt_f) {
                 float feq[9], src[9], sv[9];
                 static_for<0, 9>([&](auto K) {
@@ -650,7 +655,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
                 mrt_collide(f, feq, src, sv);
                 static_for<0, 9>([&](auto K) {
                     constexpr int k = decltype(K)::value;
-                    Stor<T>::st(fo, (long long)k * N, f[k]);
+                    Stor<T>::st(fo, (long long)(k * Nu), f[k]);
                 });
             } else {
                 const float a = 1.0f - 0.5f * s2;
@@ -660,7 +665,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
                     const float feq = Wk(k) * (p3 + rho * (3.0f * cu + 4.5f * cu * cu)) - (k == 0 ? 3.0f * pres : 0.0f);
                     float sk = 3.0f * cdot(k, Fx, Fy);
                     if (VARRHO) sk += ugr + 3.0f * (cu * cdot(k, grx, gry) - (1.0f / 3.0f) * ugr);
-                    Stor<T>::st(fo, (long long)k * N, f[k] + s2 * (feq - f[k]) + a * Wk(k) * sk);
+                    Stor<T>::st(fo, (long long)(k * Nu), f[k] + s2 * (feq - f[k]) + a * Wk(k) * sk);
                 });
             }
         }
@@ -694,14 +699,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
             } else {
                 Rf = Rf_psi;
             }
-            // dR = R + (R - R_prev)/2 exact in float-float, minus the multiplier part of R_prev
+            // dR = R + (R - R_prev)/2 minus the multiplier part of R_prev; exact in float-float
+            // for the surfactant (its total is conserved to round-off), plain float for phi
             if (A.first) {
                 dR = {Rf, 0.0f};
+            } else if (s == 0) {
+                dR = {1.5f * Rf - 0.5f * Rp_phi - lam_half * hprime(php_self, P), 0.0f};
             } else {
-                const ff t = two_sum(Rf, s == 0 ? -Rp_phi : -Rp_psi);
-                dR = ff_add_f(ff_scale_pow2(t, 0.5f), Rf);
-                if (s == 0) dR = ff_add_f(dR, -lam_half * hprime(php_self, P));
-                else dR = ff_add(dR, mub_half);
+                const ff t = two_sum(Rf, -Rp_psi);
+                dR = ff_add(ff_add_f(ff_scale_pow2(t, 0.5f), Rf), mub_half);
             }
             const ff mstar = ff_add(cff, dR);
             const float isc = s == 0 ? isc_phi : isc_psi;
@@ -746,7 +752,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
                 mrt_collide(g, geq, src, sv);
                 static_for<1, 9>([&](auto K) {
                     constexpr int k = decltype(K)::value;
-                    Stor<T>::st(dout, (long long)(k - 1) * N, g[k] + Wk(k) * shift);
+                    Stor<T>::st(dout, (long long)((k - 1) * (unsigned)N), g[k] + Wk(k) * shift);
                 });
             } else {
                 const float a = 1.0f - 0.5f * s1;
@@ -755,7 +761,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
                     constexpr int k = decltype(K)::value;
                     const float geq = Wk(k) * (ec + cdot(k, cux, cuy));
                     const float gk = g[k] + s1 * (geq - g[k]) + a * Wk(k) * cdot(k, ax, ay);
-                    Stor<T>::st(dout, (long long)(k - 1) * N, gk + Wk(k) * shift);
+                    Stor<T>::st(dout, (long long)((k - 1) * (unsigned)N), gk + Wk(k) * shift);
                 });
             }
             float2 mo;
