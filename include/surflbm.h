@@ -181,6 +181,70 @@ slbm_status slbm_read_totals(slbm_domain* d, slbm_totals* t);
 slbm_status slbm_read_fields_noalloc(slbm_domain* d, double* phi, double* psi, double* ux, double* uy,
                                      double* p, slbm_totals* totals);
 
+/* ------------------------------------------------------------------------------
+ * Batches: many independent domains (instances; grid sizes, parameters and walls may
+ * all differ, precision may not) advanced together by one launch of a persistent
+ * tile-queue kernel per time step.  Every instance follows exactly the update of
+ * slbm_step (Sec. 3; its global multipliers are reduced per instance in a fixed
+ * order), so a batch gives the same fields as stepping each instance alone up to the
+ * rounding of the reduction order.  Steps are replayed from a captured CUDA graph of
+ * graph_steps launches.  Instances are numbered 0 .. count-1.
+ * ---------------------------------------------------------------------------- */
+typedef struct slbm_batch slbm_batch;
+
+/* One wall of one instance (see slbm_set_walls). */
+typedef struct {
+    double theta0_deg, beta_sg, beta_sl, u_x;
+} slbm_wall_spec;
+
+/* params: count instances; walls: 2 * count entries (bottom, top of each instance), or
+ * NULL for neutral walls.  stream: a cudaStream_t, or NULL for a stream the batch
+ * creates and owns (graph capture needs a non-default stream).  Allocates the state of
+ * every instance.  Errors: EINVAL (message in slbm_batch_last_error(NULL)), ENOMEM, ECUDA. */
+slbm_status slbm_create_batch(const slbm_params* params, const slbm_wall_spec* walls, int count, void* stream,
+                              slbm_batch** out);
+
+/* Initial fields of instance idx (as slbm_init_fields); the instance becomes active and
+ * its time level 0 is the batch's current step. */
+slbm_status slbm_batch_init_fields(slbm_batch* b, int idx, const double* phi, const double* psi);
+
+/* Tiling of the tile queue: each instance is cut into strips of 64 columns and bands of
+ * about band_rows rows (>= 8); ctas_per_sm (1 or 2) resident CTAs per SM take pieces
+ * from the queue; graph_steps launches per captured graph. */
+slbm_status slbm_batch_set_tiling(slbm_batch* b, int band_rows, int ctas_per_sm, int graph_steps);
+
+/* Times the candidate tilings (band_rows 16..256, 1 or 2 CTAs per SM) on this batch and
+ * keeps the fastest; the choice is read from / appended to the JSON file cache_path
+ * (may be NULL), keyed by precision, instance count, total cells and the size list.
+ * The timed steps are real steps of every active instance (8 per candidate). */
+slbm_status slbm_batch_autotune(slbm_batch* b, const char* cache_path, int* band_rows_out, int* ctas_out);
+
+/* nsteps time steps of every active instance (asynchronous on the batch's stream). */
+slbm_status slbm_batch_step(slbm_batch* b, long long nsteps);
+
+/* Steps the active instances until each one's residual (max over phi and psi of
+ * ||x^n - x^{n-K}||_2 / (K ||x^n||_2), K = check_every) falls below tol, retiring each
+ * as it converges, or until max_steps more steps.  steps_out[i] (count entries): the
+ * instance's step count at convergence, -1 if it did not converge, 0 if it was inactive. */
+slbm_status slbm_batch_run_to_equilibrium(slbm_batch* b, double tol, long long max_steps, int check_every,
+                                          long long* steps_out);
+
+/* nsteps steps of instance idx alone with its own launches (as slbm_step), keeping the
+ * batch's step bookkeeping consistent; the per-instance-launch baseline of the batch. */
+slbm_status slbm_batch_step_instance(slbm_batch* b, int idx, long long nsteps);
+
+/* Fields / totals of instance idx at its current time level (as slbm_read_fields /
+ * slbm_read_totals; synchronise). */
+slbm_status slbm_batch_read_fields(slbm_batch* b, int idx, double* phi, double* psi, double* ux, double* uy,
+                                   double* p);
+slbm_status slbm_batch_read_totals(slbm_batch* b, int idx, slbm_totals* t);
+
+/* Number of active instances; flags (count ints, may be NULL) receives 1 / 0 each. */
+int slbm_batch_active(const slbm_batch* b, int* flags);
+size_t slbm_batch_device_bytes(const slbm_batch* b);
+const char* slbm_batch_last_error(const slbm_batch* b);
+void slbm_batch_destroy(slbm_batch* b);
+
 /* Bytes of device memory the domain holds. */
 size_t slbm_device_bytes(const slbm_domain* d);
 

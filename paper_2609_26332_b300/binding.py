@@ -41,6 +41,11 @@ class Params(ctypes.Structure):
     ]
 
 
+class WallSpec(ctypes.Structure):
+    _fields_ = [("theta0_deg", ctypes.c_double), ("beta_sg", ctypes.c_double), ("beta_sl", ctypes.c_double),
+                ("u_x", ctypes.c_double)]
+
+
 class Totals(ctypes.Structure):
     _fields_ = [
         ("step", ctypes.c_longlong), ("Q_phi", ctypes.c_double), ("H", ctypes.c_double),
@@ -76,6 +81,28 @@ def _load():
     for name in ("slbm_create_domain", "slbm_set_walls", "slbm_init_fields", "slbm_step",
                  "slbm_read_fields", "slbm_read_totals"):
         getattr(L, name).restype = ctypes.c_int
+    # batches
+    L.slbm_create_batch.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(WallSpec), i, vp, ctypes.POINTER(vp)]
+    L.slbm_batch_init_fields.argtypes = [vp, i, dp, dp]
+    L.slbm_batch_set_tiling.argtypes = [vp, i, i, i]
+    L.slbm_batch_autotune.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.slbm_batch_step.argtypes = [vp, ll]
+    L.slbm_batch_run_to_equilibrium.argtypes = [vp, d, ll, i, ctypes.POINTER(ll)]
+    L.slbm_batch_step_instance.argtypes = [vp, i, ll]
+    L.slbm_batch_read_fields.argtypes = [vp, i, dp, dp, dp, dp, dp]
+    L.slbm_batch_read_totals.argtypes = [vp, i, ctypes.POINTER(Totals)]
+    for name in ("slbm_create_batch", "slbm_batch_init_fields", "slbm_batch_set_tiling", "slbm_batch_autotune",
+                 "slbm_batch_step", "slbm_batch_run_to_equilibrium", "slbm_batch_step_instance",
+                 "slbm_batch_read_fields", "slbm_batch_read_totals"):
+        getattr(L, name).restype = ctypes.c_int
+    L.slbm_batch_active.argtypes = [vp, ctypes.POINTER(i)]
+    L.slbm_batch_active.restype = i
+    L.slbm_batch_device_bytes.argtypes = [vp]
+    L.slbm_batch_device_bytes.restype = ctypes.c_size_t
+    L.slbm_batch_last_error.argtypes = [vp]
+    L.slbm_batch_last_error.restype = ctypes.c_char_p
+    L.slbm_batch_destroy.argtypes = [vp]
+    L.slbm_batch_destroy.restype = None
     return L
 
 
@@ -197,3 +224,90 @@ class Domain:
 
 def version():
     return lib.slbm_version().decode()
+
+
+class Batch:
+    """Many domains stepped together by the batch tile-queue kernel (see slbm_create_batch)."""
+
+    def __init__(self, params_list, walls=None, stream=None):
+        n = len(params_list)
+        self.count = n
+        self.dims = [(p.ny, p.nx) for p in params_list]
+        P = (Params * n)(*params_list)
+        W = None
+        if walls is not None:
+            flat = []
+            for (bottom, top) in walls:
+                flat += [WallSpec(*bottom), WallSpec(*top)]
+            W = (WallSpec * (2 * n))(*flat)
+        self._h = ctypes.c_void_p()
+        st = lib.slbm_create_batch(P, W, n, _stream_handle(stream), ctypes.byref(self._h))
+        if st != SLBM_OK:
+            raise SlbmError(st, lib.slbm_batch_last_error(None).decode())
+
+    def _check(self, st):
+        if st != SLBM_OK:
+            raise SlbmError(st, lib.slbm_batch_last_error(self._h).decode())
+
+    def init_fields(self, idx, phi, psi=None):
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        if phi.shape != self.dims[idx]:
+            raise ValueError("phi must have shape (ny, nx) of the instance")
+        psi = None if psi is None else np.ascontiguousarray(psi, dtype=np.float64)
+        self._check(lib.slbm_batch_init_fields(self._h, int(idx), _dptr(phi), _dptr(psi)))
+
+    def set_tiling(self, band_rows=64, ctas_per_sm=2, graph_steps=32):
+        self._check(lib.slbm_batch_set_tiling(self._h, int(band_rows), int(ctas_per_sm), int(graph_steps)))
+
+    def autotune(self, cache_path=None):
+        br, cs = ctypes.c_int(), ctypes.c_int()
+        self._check(lib.slbm_batch_autotune(self._h, cache_path.encode() if cache_path else None,
+                                            ctypes.byref(br), ctypes.byref(cs)))
+        return br.value, cs.value
+
+    def step(self, n=1):
+        self._check(lib.slbm_batch_step(self._h, int(n)))
+
+    def step_instance(self, idx, n=1):
+        self._check(lib.slbm_batch_step_instance(self._h, int(idx), int(n)))
+
+    def run_to_equilibrium(self, tol, max_steps, check_every=100):
+        out = (ctypes.c_longlong * self.count)()
+        self._check(lib.slbm_batch_run_to_equilibrium(self._h, float(tol), int(max_steps), int(check_every), out))
+        return np.array(out[:], dtype=np.int64)
+
+    def read_fields(self, idx, which=("phi", "psi", "ux", "uy", "p")):
+        ny, nx = self.dims[idx]
+        out = {k: np.empty((ny, nx), dtype=np.float64) for k in which}
+        ptrs = [_dptr(out.get(k)) for k in ("phi", "psi", "ux", "uy", "p")]
+        self._check(lib.slbm_batch_read_fields(self._h, int(idx), *ptrs))
+        return out
+
+    def read_totals(self, idx, check=True):
+        t = Totals()
+        st = lib.slbm_batch_read_totals(self._h, int(idx), ctypes.byref(t))
+        if check:
+            self._check(st)
+        return {name: getattr(t, name) for name, _ in Totals._fields_}
+
+    def active(self):
+        flags = (ctypes.c_int * self.count)()
+        lib.slbm_batch_active(self._h, flags)
+        return np.array(flags[:], dtype=bool)
+
+    def close(self):
+        if self._h:
+            lib.slbm_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

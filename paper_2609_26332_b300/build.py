@@ -11,8 +11,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libsurflbm.so")
-SOURCES = ["surflbm_api.cu"]
-HEADERS = ["surflbm_device.cuh", "surflbm_step.cuh"]
+SOURCES = ["surflbm_api.cu", "surflbm_batch.cu"]
+HEADERS = ["surflbm_device.cuh", "surflbm_step.cuh", "surflbm_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -75,32 +75,7 @@ size_t elem_size(int prec) { return prec == SLBM_FP32 ? 4 : 2; }
 
 }  // namespace
 
-struct slbm_domain {
-    slbm_params p;
-    cudaStream_t stream = nullptr;
-    Phys phys;
-    double beta, kappa, lambda_s, W, kT, phi_b, M_phi, M_0;
-    double wall_theta[2] = {90.0, 90.0}, wall_bsg[2] = {0, 0}, wall_bsl[2] = {0, 0}, wall_u[2] = {0, 0};
-    long long N = 0;
-    dim3 grid;
-    long long total = 0;   // strips * ny, the rows the CTAs share out
-    int cur = 0;
-    long long n = 0;
-    bool initialised = false;
-    void* f[2] = {nullptr, nullptr};
-    void* gd[2] = {nullptr, nullptr};
-    void* hd[2] = {nullptr, nullptr};
-    float2* gm[2] = {nullptr, nullptr};
-    float2* hm[2] = {nullptr, nullptr};
-    float* php[2] = {nullptr, nullptr};
-    void* hist = nullptr;
-    double* partials = nullptr;
-    unsigned int* counter = nullptr;
-    Rec* recs = nullptr;  // [0], [1]: ring by step parity; [2]: diagnostic level; [3]: zeros
-    double* fields = nullptr;  // 5 N doubles, allocated on first read
-    size_t bytes = 0;
-    std::string err = "no error";
-};
+#include "surflbm_internal.cuh"
 
 namespace {
 
@@ -217,13 +192,13 @@ cudaError_t prepare_kernels() {
     static cudaError_t done = cudaErrorNotReady;
     if (done == cudaErrorNotReady) {
         const int sm = (int)smem_bytes<T>();
-        done = cudaFuncSetAttribute(step_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        done = cudaFuncSetAttribute(step_kernel<T, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(step_kernel<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            done = cudaFuncSetAttribute(step_kernel<T, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(step_kernel<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            done = cudaFuncSetAttribute(step_kernel<T, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(step_kernel<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            done = cudaFuncSetAttribute(step_kernel<T, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     }
     return done;
 }
@@ -237,11 +212,11 @@ cudaError_t launch_step(slbm_domain* d, bool diag) {
     const bool var = a.P.var_nu || a.P.rho_l != a.P.rho_g;
     const size_t sm = smem_bytes<T>();
     if (diag) {
-        if (var) step_kernel<T, true, true><<<d->grid, NTHREADS, sm, d->stream>>>(a);
-        else step_kernel<T, true, false><<<d->grid, NTHREADS, sm, d->stream>>>(a);
+        if (var) step_kernel<T, true, true, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, BatchArgs{});
+        else step_kernel<T, true, false, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, BatchArgs{});
     } else {
-        if (var) step_kernel<T, false, true><<<d->grid, NTHREADS, sm, d->stream>>>(a);
-        else step_kernel<T, false, false><<<d->grid, NTHREADS, sm, d->stream>>>(a);
+        if (var) step_kernel<T, false, true, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, BatchArgs{});
+        else step_kernel<T, false, false, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, BatchArgs{});
     }
     return cudaGetLastError();
 }
@@ -250,7 +225,7 @@ template <class T>
 int resident_ctas_per_sm() {
     int n = 0;
     if (prepare_kernels<T>() != cudaSuccess) return 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<T, false, false>, NTHREADS, smem_bytes<T>()) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<T, false, false, false>, NTHREADS, smem_bytes<T>()) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
@@ -338,8 +313,8 @@ cudaError_t launch_diag_noalloc(slbm_domain* d, unsigned char* scratch, double* 
     a.o_phi = o[0]; a.o_psi = o[1]; a.o_ux = o[2]; a.o_uy = o[3]; a.o_p = o[4];
     const bool var = a.P.var_nu || a.P.rho_l != a.P.rho_g;
     const size_t sm = smem_bytes<T>();
-    if (var) step_kernel<T, true, true><<<d->grid, NTHREADS, sm, d->stream>>>(a);
-    else step_kernel<T, true, false><<<d->grid, NTHREADS, sm, d->stream>>>(a);
+    if (var) step_kernel<T, true, true, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, BatchArgs{});
+    else step_kernel<T, true, false, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, BatchArgs{});
     return cudaGetLastError();
 }
 

@@ -95,6 +95,33 @@ struct StepArgs {
     Phys P;
 };
 
+// One instance of a batch (device memory, read-only during a launch).
+struct InstDesc {
+    const void* f[2]; const void* gd[2]; const void* hd[2];      // ping-pong population buffers
+    const float2* gm[2]; const float2* hm[2]; const float* php[2];
+    void* hist;
+    Rec* recs;                 // [0], [1]: ring by step parity; [2]: diagnostic; [3]: zeros
+    double* partials;          // npieces * NPART partial sums of the current launch
+    unsigned int* counter;     // pieces of this instance finished in the current launch
+    int nx, ny, npieces, pad;
+    long long N;
+    long long G0;              // batch step counter at this instance's time level 0
+    Phys P;
+};
+// One piece of the batch tile queue: rows [y0, y1) of strip `strip` of instance `inst`;
+// `slot` is the piece's index among its instance's pieces.
+struct Piece {
+    int inst, strip, y0, y1, slot, pad0, pad1, pad2;
+};
+struct BatchArgs {
+    const InstDesc* inst;
+    const Piece* pieces;
+    int npieces;
+    unsigned int* queue;       // next piece (reset by the last CTA of each launch)
+    unsigned int* done;        // CTAs finished in this launch
+    long long* G;              // batch step counter, advanced by the last CTA of each launch
+};
+
 __device__ __forceinline__ int wrapx(int x, int nx) {
     x %= nx;
     return x < 0 ? x + nx : x;
@@ -155,13 +182,35 @@ __device__ __forceinline__ ff warp_sum_ff(ff v) {
     return v;
 }
 
-// Block reduction of NPART float-float accumulators into partials[blockIdx], then the
-// last block reduces all partials in fixed order and resolves the multipliers.
-template <class T>
-__device__ void finish_reduction(ff (&acc)[NPART], const StepArgs<T>& A, bool diag) {
+// The time-level record from the reduced sums: lambda_phi (Eq. eq15, or the target reading),
+// M_psi mubar_psi = -sum R_psi / N (Eq. AC_psi with the stored free reaction terms), H, H0.
+__device__ __forceinline__ Rec resolve_rec(const Phys& P, int first, const Rec* rec_prev, const double* tot, bool diag) {
+    Rec r = {};
+    r.S1 = tot[P_S1];
+    r.S2 = tot[P_S2];
+    r.S3 = tot[P_S3];
+    r.Q = tot[P_Q];
+    r.phi_tot = tot[P_PHI];
+    r.psi_tot = tot[P_PSI];
+    r.kin = tot[P_KIN];
+    r.clamps = tot[P_CLAMP];
+    r.range = tot[P_RANGE];
+    r.H = P.linear ? r.phi_tot : 0.5 * P.Nd + 0.5 * r.Q;
+    r.H0 = first ? r.H : rec_prev->H0;
+    double lam = 0.0;
+    if (r.S2 > 0.0) {
+        lam = r.S1 / r.S2;
+        if (P.target && P.M_phi_d > 0.0) lam = (r.S1 + (r.H0 - r.H) / P.M_phi_d) / r.S2;
+    }
+    r.lam = lam;
+    r.mpsi_mubar = P.psi_on ? -r.S3 / P.Nd : 0.0;
+    r.a = diag ? 0.0 : (first ? 1.0 : 1.5);
+    return r;
+}
+
+// CTA sum of NPART float-float accumulators; the FP64 result is in s_blk (all threads).
+__device__ __forceinline__ void block_sum(ff (&acc)[NPART], double* s_blk) {
     __shared__ double s_w[NPART][NTHREADS / 32];
-    __shared__ double s_tot[NPART];
-    __shared__ bool s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NPART; ++q) {
@@ -169,54 +218,47 @@ __device__ void finish_reduction(ff (&acc)[NPART], const StepArgs<T>& A, bool di
         if (lane == 0) s_w[q][warp] = ff_to_d(v);
     }
     __syncthreads();
+    if (threadIdx.x < NPART) {
+        double t = 0.0;
+        for (int w = 0; w < NTHREADS / 32; ++w) t += s_w[threadIdx.x][w];
+        s_blk[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+// Partial sums of `nparts` producers (slot-major, NPART each) reduced in a fixed order by
+// the calling CTA: warp w sums quantities w, w + 8 with lanes striding the slots.
+__device__ __forceinline__ void ordered_sum(const double* partials, int nparts, double* s_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = warp; q < NPART; q += NTHREADS / 32) {
+        double t = 0.0;
+        for (int b = lane; b < nparts; b += 32) t += ((volatile const double*)partials)[(long long)b * NPART + q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) s_tot[q] = t;
+    }
+    __syncthreads();
+}
+
+// Single domain: block partials to partials[blockIdx], then the last CTA to finish
+// reduces all of them in fixed order and resolves the record of the time level.
+template <class T>
+__device__ void finish_reduction(ff (&acc)[NPART], const StepArgs<T>& A, bool diag) {
+    __shared__ double s_blk[NPART], s_tot[NPART];
+    __shared__ bool s_last;
+    block_sum(acc, s_blk);
     const int nblocks = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-    if (threadIdx.x < NPART) {
-        double s = 0.0;
-        for (int w = 0; w < NTHREADS / 32; ++w) s += s_w[threadIdx.x][w];
-        A.partials[(long long)bid * NPART + threadIdx.x] = s;
-    }
+    if (threadIdx.x < NPART) A.partials[(long long)bid * NPART + threadIdx.x] = s_blk[threadIdx.x];
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned prev = atomicAdd(A.counter, 1u);
-        s_last = (prev == (unsigned)(nblocks - 1));
-    }
+    if (threadIdx.x == 0) s_last = (atomicAdd(A.counter, 1u) == (unsigned)(nblocks - 1));
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // fixed-order reduction: warp w sums quantities w, w + 8, lanes stride the blocks
-    for (int q = warp; q < NPART; q += NTHREADS / 32) {
-        double s = 0.0;
-        for (int b = lane; b < nblocks; b += 32) s += ((volatile double*)A.partials)[(long long)b * NPART + q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) s_tot[q] = s;
-    }
-    __syncthreads();
+    ordered_sum(A.partials, nblocks, s_tot);
     if (threadIdx.x == 0) {
-        const Phys& P = A.P;
-        Rec r = {};
-        r.S1 = s_tot[P_S1];
-        r.S2 = s_tot[P_S2];
-        r.S3 = s_tot[P_S3];
-        r.Q = s_tot[P_Q];
-        r.phi_tot = s_tot[P_PHI];
-        r.psi_tot = s_tot[P_PSI];
-        r.kin = s_tot[P_KIN];
-        r.clamps = s_tot[P_CLAMP];
-        r.range = s_tot[P_RANGE];
-        r.H = P.linear ? r.phi_tot : 0.5 * P.Nd + 0.5 * r.Q;
-        r.H0 = A.first ? r.H : A.rec_prev->H0;
-        double lam = 0.0;
-        if (r.S2 > 0.0) {
-            lam = r.S1 / r.S2;
-            if (P.target && P.M_phi_d > 0.0) lam = (r.S1 + (r.H0 - r.H) / P.M_phi_d) / r.S2;
-        }
-        r.lam = lam;
-        r.mpsi_mubar = P.psi_on ? -r.S3 / P.Nd : 0.0;
-        r.a = diag ? 0.0 : (A.first ? 1.0 : 1.5);
-        *A.rec_out = r;
+        *A.rec_out = resolve_rec(A.P, A.first, A.rec_prev, s_tot, diag);
         *A.counter = 0u;
         __threadfence();
     }
@@ -255,8 +297,8 @@ __device__ __forceinline__ void static_for(F&& f) {
 // VARRHO = false: uniform density and viscosity (no density-gradient terms).
 // Work split: the strips x rows of the grid, ordered strip-major, are cut into gridDim.x
 // contiguous ranges of equal length; a CTA marches its range (one or two strip pieces).
-template <class T, bool DIAG, bool VARRHO>
-__global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) {
+template <class T, bool DIAG, bool VARRHO, bool BATCH>
+__global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, const BatchArgs B) {
     extern __shared__ __align__(16) unsigned char smem[];
     int* sK = (int*)smem;
     float2* sMT = (float2*)(smem + SM_K);
@@ -269,36 +311,59 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
     unsigned char* sStg = smem + SM_K + SM_MT + SM_P + SM_M;
     using ST = Staging<T>;
 
-    const Phys& P = A.P;
-    const int nx = A.nx, ny = A.ny;
-    const long long N = A.N;
+    // physical parameters: the kernel argument for one domain, a shared copy of the
+    // current instance's parameters in batch mode
+    __shared__ Phys sP;
+    const Phys& P = BATCH ? sP : A.P;
     const int tid = threadIdx.x;
     const float sc_phi = (float)(1u << SFIX_PHI), sc_psi = 2147483648.0f;
     const float isc_phi = 1.0f / sc_phi, isc_psi = 1.0f / sc_psi;
-    const float inv_rho_l = 1.0f / P.rho_l;
 
-    // deferred multiplier terms of time level n-1 (FP64 only here, once per thread)
-    const Rec rp = *A.rec_prev;
-    const float qcoef = (float)(rp.a * P.M_phi_d * rp.lam);
-    ff cuni;
-    {
+    // piece context: grid, state buffers, time level (set per domain or per batch piece)
+    int nx = A.nx, ny = A.ny, first = A.first;
+    long long N = A.N;
+    const T* f_in = A.f_in; const T* gd_in = A.gd_in; const T* hd_in = A.hd_in;
+    const float2* gm_in = A.gm_in; const float2* hm_in = A.hm_in; const float* php_in = A.php_in;
+    T* f_out = A.f_out; T* gd_out = A.gd_out; T* hd_out = A.hd_out;
+    float2* gm_out = A.gm_out; float2* hm_out = A.hm_out; float* php_out = A.php_out;
+    T* hist = A.hist;
+    const Rec* rec_prev = A.rec_prev;
+
+    // deferred multiplier terms of time level n-1 (FP64 only here, once per piece)
+    float inv_rho_l = 0.f, qcoef = 0.f, lam_half = 0.f;
+    ff cuni = {0.f, 0.f}, mub_half = {0.f, 0.f};
+    int nsets = 1;
+    auto set_level = [&]() {
+        const Rec rp = *rec_prev;
+        inv_rho_l = 1.0f / P.rho_l;
+        qcoef = (float)(rp.a * P.M_phi_d * rp.lam);
         const double cu = rp.a * rp.mpsi_mubar;
         cuni.hi = (float)cu;
         cuni.lo = (float)(cu - (double)cuni.hi);
-    }
-    const float lam_half = (float)(0.5 * P.M_phi_d * rp.lam);
-    ff mub_half;
-    {
+        lam_half = (float)(0.5 * P.M_phi_d * rp.lam);
         const double hm = -0.5 * rp.mpsi_mubar;
         mub_half.hi = (float)hm;
         mub_half.lo = (float)(hm - (double)mub_half.hi);
-    }
+        nsets = P.psi_on ? 2 : 1;
+    };
     int range = 0;
     float clamps = 0.0f, s1acc = 0.0f, s2acc = 0.0f, kinacc = 0.0f;
     ff acc[NPART];
+    auto reset_acc = [&]() {
 #pragma unroll
-    for (int q = 0; q < NPART; ++q) acc[q] = {0.0f, 0.0f};
-    const int nsets = P.psi_on ? 2 : 1;
+        for (int q = 0; q < NPART; ++q) acc[q] = {0.0f, 0.0f};
+        range = 0;
+        clamps = s1acc = s2acc = kinacc = 0.0f;
+    };
+    auto pack_acc = [&]() {
+        acc[P_CLAMP] = {clamps, 0.0f};
+        acc[P_RANGE] = {(float)range, 0.0f};
+        acc[P_S1] = {s1acc, 0.0f};
+        acc[P_S2] = {s2acc, 0.0f};
+        acc[P_KIN] = {kinacc, 0.0f};
+    };
+    if (!BATCH) set_level();
+    reset_acc();
 
     int x0 = 0, ys = 0, ye = 0;
     bool vec = false;
@@ -325,15 +390,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
                 const long long rowoff = (long long)y * nx + ws;
                 if (q < 16 * CD) {
                     const int pl = q / CD, ch = q - pl * CD;
-                    const T* src = (pl < 8 ? A.gd_in : A.hd_in) + (long long)(pl & 7) * N + rowoff;
+                    const T* src = (pl < 8 ? gd_in : hd_in) + (long long)(pl & 7) * N + rowoff;
                     cp_async16(row + (size_t)pl * WW * sizeof(T) + ch * 16, (const unsigned char*)src + ch * 16);
                 } else if ((q -= 16 * CD) < 2 * CM) {
                     const int pl = q / CM, ch = q - pl * CM;
                     cp_async16(row + ST::D_ROW + (size_t)pl * WW * sizeof(float2) + ch * 16,
-                               (const unsigned char*)((pl == 0 ? A.gm_in : A.hm_in) + rowoff) + ch * 16);
+                               (const unsigned char*)((pl == 0 ? gm_in : hm_in) + rowoff) + ch * 16);
                 } else {
                     q -= 2 * CM;
-                    cp_async16(row + ST::D_ROW + ST::M_ROW + q * 16, (const unsigned char*)(A.php_in + rowoff) + q * 16);
+                    cp_async16(row + ST::D_ROW + ST::M_ROW + q * 16, (const unsigned char*)(php_in + rowoff) + q * 16);
                 }
             }
             cp_async_commit();
@@ -349,13 +414,13 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
                 T* dd = (T*)row;
 #pragma unroll
                 for (int pl = 0; pl < 8; ++pl) {
-                    dd[pl * WW + col] = A.gd_in[(long long)pl * N + cidx];
-                    dd[(pl + 8) * WW + col] = A.hd_in[(long long)pl * N + cidx];
+                    dd[pl * WW + col] = gd_in[(long long)pl * N + cidx];
+                    dd[(pl + 8) * WW + col] = hd_in[(long long)pl * N + cidx];
                 }
                 float2* mm = (float2*)(row + ST::D_ROW);
-                mm[col] = A.gm_in[cidx];
-                mm[WW + col] = A.hm_in[cidx];
-                ((float*)(row + ST::D_ROW + ST::M_ROW))[col] = A.php_in[cidx];
+                mm[col] = gm_in[cidx];
+                mm[WW + col] = hm_in[cidx];
+                ((float*)(row + ST::D_ROW + ST::M_ROW))[col] = php_in[cidx];
             }
         }
     };
@@ -495,10 +560,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
 
         // flow pull first (longest latency): halfway bounce-back with the moving-wall term
         float f[9];
-        const float php_self = __ldg(A.php_in + c);
+        const float php_self = __ldg(php_in + c);
         {
             const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
-            const T* fin = A.f_in;
+            const T* fin = f_in;
             const long long rm = c - gx + (long long)(y > 0 ? -nx : 0);      // row y - 1 (clamped)
             const long long r0c = c - gx;
             const long long rp1 = c - gx + (long long)(y < ny - 1 ? nx : 0);  // row y + 1 (clamped)
@@ -635,7 +700,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
                 s2 = __frcp_rn(3.0f * nu + 0.5f);
             }
             const float p3 = 3.0f * pres - 1.5f * rho * usq;
-            T* fo = A.f_out + c;
+            T* fo = f_out + c;
             const unsigned Nu = (unsigned)N;
             if (P.mrt_f) {
                 float feq[9], src[9], sv[9];
@@ -673,8 +738,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
         // ---- history of the source terms (Sec. 3, backward differences)
         const float phux = phi * ux, phuy = phi * uy, psux = psi * ux, psuy = psi * uy;
         float dphux = 0.f, dphuy = 0.f, dpsux = 0.f, dpsuy = 0.f, Rp_phi = 0.f, Rp_psi = 0.f;
-        T* hi_ = A.hist + c;
-        if (!A.first) {
+        T* hi_ = hist + c;
+        if (!first) {
             Rp_phi = Stor<T>::ld(hi_, 0);
             dphux = phux - Stor<T>::ld(hi_, 2 * N);
             dphuy = phuy - Stor<T>::ld(hi_, 3 * N);
@@ -701,7 +766,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
             }
             // dR = R + (R - R_prev)/2 minus the multiplier part of R_prev; exact in float-float
             // for the surfactant (its total is conserved to round-off), plain float for phi
-            if (A.first) {
+            if (first) {
                 dR = {Rf, 0.0f};
             } else if (s == 0) {
                 dR = {1.5f * Rf - 0.5f * Rp_phi - lam_half * hprime(php_self, P), 0.0f};
@@ -736,7 +801,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
             // the zeroth moment is carried exactly by m*; the deviations are g*_k - w_k hi(m*)
             // with the local source w_k dR folded in:  g*_k + w_k (dR - hi(m*))
             const float shift = (dR.hi + dR.lo) - mstar.hi;
-            T* dout = (s == 0 ? A.gd_out : A.hd_out) + c;
+            T* dout = (s == 0 ? gd_out : hd_out) + c;
             if (mrt) {
                 float geq[9], src[9], sv[9];
                 static_for<0, 9>([&](auto K) {
@@ -767,25 +832,20 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
             float2 mo;
             mo.x = mstar.hi;
             mo.y = mstar.lo;
-            (s == 0 ? A.gm_out : A.hm_out)[c] = mo;
+            (s == 0 ? gm_out : hm_out)[c] = mo;
             Stor<T>::st(hi_, (long long)s * N, Rf);
             Stor<T>::st(hi_, (long long)(2 + 2 * s) * N, s == 0 ? phux : psux);
             Stor<T>::st(hi_, (long long)(3 + 2 * s) * N, s == 0 ? phuy : psuy);
         }
-        A.php_out[c] = phi;
+        php_out[c] = phi;
     };
 
     // --------------------------------------------------------------- pipeline
     using I2 = std::integral_constant<int, 2>;
     using I4 = std::integral_constant<int, 4>;
-    const long long total = A.total;
-    long long lo = total * blockIdx.x / gridDim.x;
-    const long long hi = total * (blockIdx.x + 1) / gridDim.x;
-    while (lo < hi) {
-        const int strip = (int)(lo / ny);
-        ys = (int)(lo - (long long)strip * ny);
-        ye = (int)min((long long)ny, (long long)ys + (hi - lo));
-        lo += ye - ys;
+    auto march = [&](int strip, int y0, int y1) {
+        ys = y0;
+        ye = y1;
         x0 = strip * TX;
         vec = (x0 - WOFF >= 0) && (x0 - WOFF + WW <= nx) && (nx % VEC == 0);
         __syncthreads();   // the previous piece's last collide read the rings
@@ -819,13 +879,86 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A) 
             __syncthreads();
             b ^= 1;
         }
+    };
+
+    if (!BATCH) {
+        // one domain: the strips x rows, strip-major, cut into gridDim.x equal ranges
+        const long long total = A.total;
+        long long lo = total * blockIdx.x / gridDim.x;
+        const long long hi = total * (blockIdx.x + 1) / gridDim.x;
+        while (lo < hi) {
+            const int strip = (int)(lo / ny);
+            const int y0 = (int)(lo - (long long)strip * ny);
+            const int y1 = (int)min((long long)ny, (long long)y0 + (hi - lo));
+            lo += y1 - y0;
+            march(strip, y0, y1);
+        }
+        pack_acc();
+        finish_reduction<T>(acc, A, DIAG);
+        return;
     }
-    acc[P_CLAMP] = {clamps, 0.0f};
-    acc[P_RANGE] = {(float)range, 0.0f};
-    acc[P_S1] = {s1acc, 0.0f};
-    acc[P_S2] = {s2acc, 0.0f};
-    acc[P_KIN] = {kinacc, 0.0f};
-    finish_reduction<T>(acc, A, DIAG);
+
+    // batch: persistent CTAs take pieces from the tile queue; every piece is reduced on
+    // its own into its instance's slot, and the instance's last piece resolves its record
+    __shared__ int s_piece;
+    __shared__ bool s_last;
+    __shared__ double s_blk[NPART], s_tot[NPART];
+    const long long G = *B.G;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_piece = (int)atomicAdd(B.queue, 1u);
+        __syncthreads();
+        const int pi = s_piece;
+        if (pi >= B.npieces) break;
+        const Piece pc = B.pieces[pi];
+        const InstDesc* I = B.inst + pc.inst;
+        {
+            const int* src = (const int*)&I->P;
+            int* dst = (int*)&sP;
+            for (int w = tid; w < (int)(sizeof(Phys) / 4); w += NTHREADS) dst[w] = src[w];
+        }
+        nx = I->nx;
+        ny = I->ny;
+        N = I->N;
+        const long long n = G - I->G0;
+        first = n == 0;
+        const int ci = (int)(n & 1), co = ci ^ 1;
+        f_in = (const T*)I->f[ci]; gd_in = (const T*)I->gd[ci]; hd_in = (const T*)I->hd[ci];
+        gm_in = I->gm[ci]; hm_in = I->hm[ci]; php_in = I->php[ci];
+        f_out = (T*)I->f[co]; gd_out = (T*)I->gd[co]; hd_out = (T*)I->hd[co];
+        gm_out = (float2*)I->gm[co]; hm_out = (float2*)I->hm[co]; php_out = (float*)I->php[co];
+        hist = (T*)I->hist;
+        rec_prev = n == 0 ? I->recs + 3 : I->recs + ((n - 1) & 1);
+        __syncthreads();   // sP visible
+        set_level();
+        reset_acc();
+        march(pc.strip, pc.y0, pc.y1);
+        pack_acc();
+        block_sum(acc, s_blk);
+        if (tid < NPART) I->partials[(long long)pc.slot * NPART + tid] = s_blk[tid];
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_last = (atomicAdd(I->counter, 1u) == (unsigned)(I->npieces - 1));
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            ordered_sum(I->partials, I->npieces, s_tot);
+            if (tid == 0) {
+                I->recs[n & 1] = resolve_rec(P, first, rec_prev, s_tot, false);
+                *I->counter = 0u;
+                __threadfence();
+            }
+        }
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(B.done, 1u) == gridDim.x - 1) {
+            *B.queue = 0u;
+            *B.done = 0u;
+            *B.G = G + 1;
+            __threadfence();
+        }
+    }
 }
 
 #undef KR
