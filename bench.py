@@ -1,7 +1,7 @@
 """Benchmark of the coupled phase-field / surfactant / flow LBM step on B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
-                    [--workload shear|batch] [--precision fp32|fp16|bf16]
+                    [--workload shear|batch|warmstart] [--precision fp32|fp16|bf16]
 
 Workload (default): the sheared sessile drop (top wall at u_w = 0.01, 90 deg contact
 angle, psi0 = 0.02, solid-gas adsorption 0.5, tau = 0.8, eps = 4, FP32) on a
@@ -15,6 +15,13 @@ Workload 'batch': 512 sessile-drop instances of uneven seeded grids (64 x 32 to
 instance), all stepped by one persistent tile-queue launch per step replayed from a
 CUDA graph, tiling chosen by the autotuner; the same instances stepped one launch
 per instance per step are timed beside it.
+
+Workload 'warmstart': the learned warm start on 256 x 128 sessile drops.  Training
+drops (seeded parameters: contact angle U[30,150] deg, psi0 U[0.005,0.05], adsorption
+strengths U[0,1], radius U[0.25,0.35] ny) are relaxed from cold starts by the batch
+solver, the encoder-decoder is trained on the relaxed fields with the tensor-core
+kernels, and held-out drops are relaxed from cold and from warm starts; the value is
+the median ratio of cold to warm steps to equilibrium.
 
 Prints one JSON line (rank 0).  Metric: MLUPS (million lattice-node updates per
 second, whole job).  Under torchrun with N > 1 every rank steps its own replica of the
@@ -265,6 +272,66 @@ def run_batch(args, rank, world, dist):
     b.close()
 
 
+def run_warmstart(args, rank, world, dist):
+    """Steps to equilibrium, cold vs learned warm start, on held-out drops."""
+    import torch
+    from paper_2609_26332_b300 import binding as B, warmstart as WS
+    ny, nx = 128, 256
+    t0 = time.perf_counter()
+    logs = []
+    log = lambda m: (logs.append(m), print(m, file=sys.stderr, flush=True))
+    net = B.WarmStartNet(ny, nx, max_batch=args.ws_batch, seed=7 + rank)
+    train_specs = WS.drop_specs(args.ws_train, seed=1000 + rank, ny=ny, nx=nx)
+    test_specs = WS.drop_specs(args.ws_eval, seed=9000 + rank, ny=ny, nx=nx)
+    cond, targets, steps = WS.build_dataset(net, train_specs, args.ws_tol, args.ws_max_steps, log=log)
+    t_data = time.perf_counter() - t0
+    ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev[0].record()
+    hist = WS.train(net, cond, targets, args.ws_epochs, args.ws_batch, args.ws_lr, log=log)
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_train = ev[0].elapsed_time(ev[1]) / 1e3
+    t1 = time.perf_counter()
+    res = WS.evaluate(net, test_specs, args.ws_tol, args.ws_max_steps)
+    t_eval = time.perf_counter() - t1
+    both = (res["steps_cold"] > 0) & (res["steps_warm"] > 0)
+    ratio = res["steps_cold"][both] / np.maximum(res["steps_warm"][both], 1)
+    dang = np.abs(res["angle_cold"] - res["angle_warm"])[both]
+    # training throughput of the conv kernels: 3 x forward FLOPs per sample (fwd, dgrad, wgrad)
+    fwd_flops = sum(2 * 9 * ci * co * (ny >> lv) * (nx >> lv)
+                    for lv, ci, co in [(0, 16, 32), (0, 32, 32), (1, 32, 64), (1, 64, 64), (2, 64, 128),
+                                       (2, 128, 128), (3, 128, 128), (3, 128, 128), (2, 256, 128), (2, 128, 128),
+                                       (1, 192, 64), (1, 64, 64), (0, 96, 32), (0, 32, 32)])
+    train_tflops = 3 * fwd_flops * len(cond) * args.ws_epochs / t_train / 1e12
+    if rank == 0:
+        line = {
+            "metric": "steps-to-equilibrium ratio, cold / learned warm start", "value": float(np.median(ratio))
+            if len(ratio) else None, "unit": "x", "n_gpus": world, "steps": args.ws_epochs, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16-conv/f32-lbm",
+            "data": "synthetic: LBM-relaxed seeded sessile drops",
+            "config": {"workload": f"warm start, {ny}x{nx} drops, {args.ws_train} training drops, "
+                                   f"{args.ws_eval} held-out, residual tol {args.ws_tol:g}",
+                       "train_converged": int(len(cond)), "train_diverged": int((steps == -2).sum()),
+                       "train_unconverged": int((steps == -1).sum()), "epochs": args.ws_epochs,
+                       "batch": args.ws_batch},
+            "eval": {"pairs": int(both.sum()), "cold_converged": int((res["steps_cold"] > 0).sum()),
+                     "warm_converged": int((res["steps_warm"] > 0).sum()),
+                     "median_steps_cold": float(np.median(res["steps_cold"][both])) if both.any() else None,
+                     "median_steps_warm": float(np.median(res["steps_warm"][both])) if both.any() else None,
+                     "ratio_p25": float(np.quantile(ratio, 0.25)) if len(ratio) else None,
+                     "angle_diff_median_deg": float(np.median(dang)) if len(dang) else None,
+                     "angle_diff_max_deg": float(np.max(dang)) if len(dang) else None,
+                     "frac_within_0p5deg": float(np.mean(dang < 0.5)) if len(dang) else None,
+                     "accepted": int(res["accepted"].sum())},
+            "train": {"final_loss": hist[-1], "first_loss": hist[0], "seconds": t_train,
+                      "conv_tflops": train_tflops},
+            "seconds": {"dataset": t_data, "train": t_train, "eval": t_eval},
+            "gpu_launches": None,
+        }
+        print(json.dumps(line))
+    net.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -275,7 +342,14 @@ def main():
     ap.add_argument("--ny", type=int, default=2048)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="shear", choices=["shear", "batch"])
+    ap.add_argument("--workload", default="shear", choices=["shear", "batch", "warmstart"])
+    ap.add_argument("--ws-train", type=int, default=4096)
+    ap.add_argument("--ws-eval", type=int, default=256)
+    ap.add_argument("--ws-epochs", type=int, default=60)
+    ap.add_argument("--ws-batch", type=int, default=32)
+    ap.add_argument("--ws-lr", type=float, default=2e-3)
+    ap.add_argument("--ws-tol", type=float, default=1e-7)
+    ap.add_argument("--ws-max-steps", type=int, default=60000)
     ap.add_argument("--instances", type=int, default=512)
     ap.add_argument("--graph-steps", type=int, default=32)
     ap.add_argument("--tiling-cache", default=None)
@@ -298,8 +372,8 @@ def main():
     from paper_2609_26332_b300 import build as _build
     _build.build()
     from paper_2609_26332_b300 import binding as B
-    if args.workload == "batch":
-        run_batch(args, rank, world, dist)
+    if args.workload in ("batch", "warmstart"):
+        (run_batch if args.workload == "batch" else run_warmstart)(args, rank, world, dist)
         if dist:
             dist.destroy_process_group()
         return

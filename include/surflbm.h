@@ -87,6 +87,8 @@ typedef struct {
     int multiplier;          /* slbm_multiplier                                         */
     int precision;           /* slbm_precision                                          */
     int psi_on;              /* 0: surfactant transport disabled (psi == 0)             */
+    int wall_saturation;     /* 1: solid tensions capped at half their clean values      */
+                             /* (Remark 1; inactive while 1 + beta ln(1 - psi_w) > 1/2)  */
 } slbm_params;
 
 /* Quantities reduced in FP64 over the whole grid at one time level. */
@@ -130,6 +132,10 @@ slbm_status slbm_set_walls(slbm_domain* d, int wall, double theta0_deg,
  * and sets the state to the equilibria at rest (u = 0, p = 0) of those fields at
  * step 0, as the pre-collision populations of time 0.  Resets the step counter. */
 slbm_status slbm_init_fields(slbm_domain* d, const double* phi, const double* psi);
+
+/* As slbm_init_fields with phi and psi in DEVICE memory of this domain's device
+ * (row-major [ny][nx] doubles); used to start from a state computed on the GPU. */
+slbm_status slbm_init_fields_device(slbm_domain* d, const double* phi, const double* psi);
 
 /* Queues nsteps >= 0 time steps on the domain's stream (asynchronous).  Returns the
  * status of previously completed work only when it is already known (ECUDA on a
@@ -207,6 +213,8 @@ slbm_status slbm_create_batch(const slbm_params* params, const slbm_wall_spec* w
 /* Initial fields of instance idx (as slbm_init_fields); the instance becomes active and
  * its time level 0 is the batch's current step. */
 slbm_status slbm_batch_init_fields(slbm_batch* b, int idx, const double* phi, const double* psi);
+/* As slbm_batch_init_fields with phi, psi in device memory (slbm_init_fields_device). */
+slbm_status slbm_batch_init_fields_device(slbm_batch* b, int idx, const double* phi, const double* psi);
 
 /* Tiling of the tile queue: each instance is cut into strips of 64 columns and bands of
  * about band_rows rows (>= 8); ctas_per_sm (1 or 2) resident CTAs per SM take pieces
@@ -225,7 +233,9 @@ slbm_status slbm_batch_step(slbm_batch* b, long long nsteps);
 /* Steps the active instances until each one's residual (max over phi and psi of
  * ||x^n - x^{n-K}||_2 / (K ||x^n||_2), K = check_every) falls below tol, retiring each
  * as it converges, or until max_steps more steps.  steps_out[i] (count entries): the
- * instance's step count at convergence, -1 if it did not converge, 0 if it was inactive. */
+ * instance's step count at convergence, -1 if it did not converge, -2 if its fields
+ * became non-finite (the instance diverged; it is retired at the check that sees it),
+ * 0 if it was inactive. */
 slbm_status slbm_batch_run_to_equilibrium(slbm_batch* b, double tol, long long max_steps, int check_every,
                                           long long* steps_out);
 

@@ -142,6 +142,18 @@ class Oracle:
         e = self.p.psi_clamp
         return np.clip(psi, e, 1.0 - e)
 
+    def _wall_tension_factors(self, w, L):
+        """t_a = sigma_s,a / sigma_s,a,0 - 1 of wall w for a in (sg, sl), and whether the
+        logarithmic law is in force: t_a = beta_a L (Eq. langmuir, L = ln(1 - psi)), capped
+        at -1/2 where the tension would fall below half its clean value (Remark 1) when
+        p.saturation; on_a = 1 where dt_a/dpsi = -beta_a / (1 - psi), 0 on the cap."""
+        wl = self.p.walls[w]
+        t_sg, t_sl = wl.beta_sg * L, wl.beta_sl * L
+        if not self.p.saturation:
+            return t_sg, t_sl, 1.0, 1.0
+        on_sg, on_sl = t_sg > -0.5, t_sl > -0.5
+        return np.where(on_sg, t_sg, -0.5), np.where(on_sl, t_sl, -0.5), on_sg, on_sl
+
     def _wall_ghosts(self, phi, psi):
         """Ghost rows (bottom at j = -1, top at j = ny) from Eq. boundary (reading c2)."""
         d, p = self.d, self.p
@@ -150,8 +162,13 @@ class Oracle:
             ph, ps = phi[row], psi[row]
             psc = self._clamp(ps) if p.psi_on else ps
             L = np.log1p(-psc)
-            dfdphi = -(d.wall_cos[w] + L * d.wall_A[w]) * self._gprime(ph)
-            dfdpsi = (d.wall_A[w] * self._g(ph) - 0.5 * d.wall_B[w]) / (1.0 - psc)
+            t_sg, t_sl, on_sg, on_sl = self._wall_tension_factors(w, L)
+            # f_w = (1/2 - g) sigma_sg + (1/2 + g) sigma_sl with sigma_s,a = sigma_s,a,0 (1 + t_a)
+            # and sigma_sg,0 - sigma_sl,0 written as sigma cos(theta0) (Eq. fw0, Eq. langmuir)
+            dfdphi = -(d.wall_cos[w] + d.wall_sg0[w] * t_sg - d.wall_sl0[w] * t_sl) * self._gprime(ph)
+            g = self._g(ph)
+            dfdpsi = -((0.5 - g) * d.wall_sg0[w] * p.walls[w].beta_sg * on_sg
+                       + (0.5 + g) * d.wall_sl0[w] * p.walls[w].beta_sl * on_sl) / (1.0 - psc)
             phiG = ph - dfdphi / d.kappa if d.kappa > 0 else ph.copy()
             psiG = ps - dfdpsi / d.lambda_s if (d.lambda_s > 0 and p.psi_on) else ps.copy()
             out.append((phiG, psiG))
@@ -397,6 +414,8 @@ class Oracle:
             ps = self._clamp(psi[row]) if p.psi_on else psi[row]
             L = np.log1p(-ps)
             s_sum = 16.0 * p.sigma / 15.0
-            fw = -(d.wall_cos[w] + L * d.wall_A[w]) * self._g(ph) + 0.5 * L * d.wall_B[w] + 0.5 * s_sum
+            t_sg, t_sl, _, _ = self._wall_tension_factors(w, L)
+            fw = (-(d.wall_cos[w] + d.wall_sg0[w] * t_sg - d.wall_sl0[w] * t_sl) * self._g(ph)
+                  + 0.5 * (d.wall_sg0[w] * t_sg + d.wall_sl0[w] * t_sl) + 0.5 * s_sum)
             E += float(np.sum(fw))
         return E

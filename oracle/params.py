@@ -71,6 +71,7 @@ class OracleParams:
     psi_on: bool = True             # False: surfactant transport disabled, psi == 0
     walls: list = field(default_factory=lambda: [Wall(), Wall()])  # [bottom, top]
     psi_clamp: float = 1e-12
+    saturation: bool = True         # Remark 1 cap: sigma_s,alpha >= sigma_s,alpha,0 / 2 (reading c20)
 
 
 @dataclass
@@ -89,6 +90,8 @@ class Derived:
     wall_A: list   # sigma_sg0 beta_sg - sigma_sl0 beta_sl per wall
     wall_B: list   # sigma_sg0 beta_sg + sigma_sl0 beta_sl per wall
     wall_cos: list  # sigma cos(theta0) per wall
+    wall_sg0: list  # clean solid-gas tension sigma_sg,0 per wall
+    wall_sl0: list  # clean solid-liquid tension sigma_sl,0 per wall
 
 
 def derive(p: OracleParams) -> Derived:
@@ -110,7 +113,7 @@ def derive(p: OracleParams) -> Derived:
     M_0 = p.eta_psi * CS2 * (p.tau_h - 0.5) - p.M_psi * lam_s
     nu_l = CS2 * (p.tau_f - 0.5)
     nu_g = CS2 * ((p.tau_f_gas if p.tau_f_gas > 0 else p.tau_f) - 0.5)
-    A, B, C = [], [], []
+    A, B, C, SG, SL = [], [], [], [], []
     for w in p.walls:
         c = math.cos(math.radians(w.theta0_deg))
         s_sg = p.sigma * (16.0 / 15.0 + c) / 2.0
@@ -118,7 +121,9 @@ def derive(p: OracleParams) -> Derived:
         A.append(s_sg * w.beta_sg - s_sl * w.beta_sl)
         B.append(s_sg * w.beta_sg + s_sl * w.beta_sl)
         C.append(p.sigma * c)
-    return Derived(beta, kappa, lam_s, W, kT, phi_b, M_phi, p.M_psi, M_0, nu_l, nu_g, A, B, C)
+        SG.append(s_sg)
+        SL.append(s_sl)
+    return Derived(beta, kappa, lam_s, W, kT, phi_b, M_phi, p.M_psi, M_0, nu_l, nu_g, A, B, C, SG, SL)
 
 
 def clean_solid_tensions(sigma, theta0_deg):

@@ -12,11 +12,14 @@ kernels and the whole-network gradient can be checked against it.
   beta_sg, beta_sl, psi0, area fraction) and the cell coordinates.
 * ``Net`` - the architecture (4 levels of two convs, 2 x 2 average pooling, nearest
   upsampling with skip concatenation, a 1 x 1 head), its loss and the gradient of the
-  loss by reverse-mode differentiation written out layer by layer.
+  loss by reverse-mode differentiation written out layer by layer.  An optional
+  rounding ``q`` (``round_bf16``) is applied wherever the GPU stores a tensor in BF16,
+  so that both sides take the same rounding decisions.
 
 Pins: ``tests/test_oracle_warmstart.py`` ties the convolution to scipy's 2-D
-correlation, the adjoints to the forward through inner-product identities, and the
-whole-network gradient to central finite differences of the loss.
+correlation, the adjoints to the forward through inner-product identities, the
+whole-network gradient to central finite differences of the loss, and ``round_bf16``
+to torch's float32 -> bfloat16 conversion.
 """
 
 import numpy as np
@@ -153,32 +156,37 @@ class Net:
     def __init__(self, flat):
         self.layers, self.head = unpack(flat)
 
-    def forward(self, cond, H, W):
-        """Head outputs [B, 2, H, W] and the activations the backward pass needs."""
+    def forward(self, cond, H, W, q=None):
+        """Head outputs [B, 2, H, W] and the activations the backward pass needs.
+
+        q: optional rounding applied to every stored activation (the input features,
+        each conv output, each pooled tensor); None = exact FP64."""
+        q = q or (lambda t: t)
         L = self.layers
         relu = lambda z: np.maximum(z, 0.0)
+        conv = lambda x, i: q(relu(conv3x3(x, *L[i])))
         a = {}
-        a["x0"] = features(cond, H, W)
-        a["y0"] = relu(conv3x3(a["x0"], *L[0]))
-        a["y1"] = relu(conv3x3(a["y0"], *L[1]))
-        a["p0"] = pool2(a["y1"])
-        a["y2"] = relu(conv3x3(a["p0"], *L[2]))
-        a["y3"] = relu(conv3x3(a["y2"], *L[3]))
-        a["p1"] = pool2(a["y3"])
-        a["y4"] = relu(conv3x3(a["p1"], *L[4]))
-        a["y5"] = relu(conv3x3(a["y4"], *L[5]))
-        a["p2"] = pool2(a["y5"])
-        a["y6"] = relu(conv3x3(a["p2"], *L[6]))
-        a["y7"] = relu(conv3x3(a["y6"], *L[7]))
+        a["x0"] = q(features(cond, H, W))
+        a["y0"] = conv(a["x0"], 0)
+        a["y1"] = conv(a["y0"], 1)
+        a["p0"] = q(pool2(a["y1"]))
+        a["y2"] = conv(a["p0"], 2)
+        a["y3"] = conv(a["y2"], 3)
+        a["p1"] = q(pool2(a["y3"]))
+        a["y4"] = conv(a["p1"], 4)
+        a["y5"] = conv(a["y4"], 5)
+        a["p2"] = q(pool2(a["y5"]))
+        a["y6"] = conv(a["p2"], 6)
+        a["y7"] = conv(a["y6"], 7)
         a["c2"] = np.concatenate([up2(a["y7"]), a["y5"]], axis=3)
-        a["y8"] = relu(conv3x3(a["c2"], *L[8]))
-        a["y9"] = relu(conv3x3(a["y8"], *L[9]))
+        a["y8"] = conv(a["c2"], 8)
+        a["y9"] = conv(a["y8"], 9)
         a["c1"] = np.concatenate([up2(a["y9"]), a["y3"]], axis=3)
-        a["y10"] = relu(conv3x3(a["c1"], *L[10]))
-        a["y11"] = relu(conv3x3(a["y10"], *L[11]))
+        a["y10"] = conv(a["c1"], 10)
+        a["y11"] = conv(a["y10"], 11)
         a["c0"] = np.concatenate([up2(a["y11"]), a["y1"]], axis=3)
-        a["y12"] = relu(conv3x3(a["c0"], *L[12]))
-        a["y13"] = relu(conv3x3(a["y12"], *L[13]))
+        a["y12"] = conv(a["c0"], 12)
+        a["y13"] = conv(a["y12"], 13)
         hw, hb = self.head
         out = a["y13"] @ hw.T + hb                      # [B, H, W, 2]
         return np.moveaxis(out, 3, 1), a
@@ -190,11 +198,18 @@ class Net:
         B, _, H, W = targets.shape
         return float(((out - targets) ** 2).sum() / (B * H * W))
 
-    def loss_grad(self, cond, targets):
-        """(loss, flat gradient) by reverse-mode differentiation."""
+    def loss_grad(self, cond, targets, q=None):
+        """(loss, flat gradient) by reverse-mode differentiation.
+
+        gz[i] is the gradient w.r.t. the pre-activation output of conv i (the ReLU mask
+        applied); the weight and bias gradients of conv i follow from gz[i] and the
+        conv's input.  q: optional rounding of every stored activation and of every
+        stored gradient tensor (gz[i], the gradients w.r.t. the concatenated and pooled
+        conv inputs); None = exact FP64."""
+        q = q or (lambda t: t)
         targets = np.asarray(targets, dtype=np.float64)
         B, _, H, W = targets.shape
-        out, a = self.forward(cond, H, W)
+        out, a = self.forward(cond, H, W, q)
         n = B * H * W
         r = out - targets
         loss = float((r ** 2).sum() / n)
@@ -203,33 +218,38 @@ class Net:
         g_hw = go.reshape(-1, 2).T @ a["y13"].reshape(-1, HEAD)
         g_hb = go.reshape(-1, 2).sum(axis=0)
         L = self.layers
-        gw = [None] * len(L)
-        gb = [None] * len(L)
+        on = lambda name: a[name] > 0                   # ReLU mask of a stored activation
+        back = lambda i, g: conv3x3_input_grad(g, L[i][0])
+        gz = [None] * len(L)
+        gz[13] = q((go @ hw) * on("y13"))
+        gz[12] = q(back(13, gz[13]) * on("y12"))
+        g_c0 = q(back(12, gz[12]) * on("c0"))           # w.r.t. the concatenation (up(y11), y1)
+        gz[11] = q(up2_adjoint(g_c0[..., :64]) * on("y11"))
+        gz[10] = q(back(11, gz[11]) * on("y10"))
+        g_c1 = q(back(10, gz[10]) * on("c1"))           # (up(y9), y3)
+        gz[9] = q(up2_adjoint(g_c1[..., :128]) * on("y9"))
+        gz[8] = q(back(9, gz[9]) * on("y8"))
+        g_c2 = q(back(8, gz[8]) * on("c2"))             # (up(y7), y5)
+        gz[7] = q(up2_adjoint(g_c2[..., :128]) * on("y7"))
+        gz[6] = q(back(7, gz[7]) * on("y6"))
+        g_p2 = q(back(6, gz[6]))                        # w.r.t. the pooled p2 (no ReLU there)
+        gz[5] = q((pool2_adjoint(g_p2) + g_c2[..., 128:]) * on("y5"))
+        gz[4] = q(back(5, gz[5]) * on("y4"))
+        g_p1 = q(back(4, gz[4]))
+        gz[3] = q((pool2_adjoint(g_p1) + g_c1[..., 128:]) * on("y3"))
+        gz[2] = q(back(3, gz[3]) * on("y2"))
+        g_p0 = q(back(2, gz[2]))
+        gz[1] = q((pool2_adjoint(g_p0) + g_c0[..., 64:]) * on("y1"))
+        gz[0] = q(back(1, gz[1]) * on("y0"))
         inputs = ["x0", "y0", "p0", "y2", "p1", "y4", "p2", "y6", "c2", "y8", "c1", "y10", "c0", "y12"]
-
-        def through_conv(i, gy):
-            """gy = d loss / d y_i (post-ReLU); returns d loss / d input of conv i."""
-            gz = gy * (a[f"y{i}"] > 0)
-            gw[i] = conv3x3_weight_grad(a[inputs[i]], gz)
-            gb[i] = gz.reshape(-1, gz.shape[3]).sum(axis=0)
-            return conv3x3_input_grad(gz, L[i][0])
-
-        g = go @ hw                                      # d loss / d y13
-        g = through_conv(13, g)                          # d / d y12
-        g = through_conv(12, g)                          # d / d c0
-        g_c0 = g
-        g = through_conv(11, up2_adjoint(g_c0[..., :64]))
-        g = through_conv(10, g)                          # d / d c1
-        g_c1 = g
-        g = through_conv(9, up2_adjoint(g_c1[..., :128]))
-        g = through_conv(8, g)                           # d / d c2
-        g_c2 = g
-        g = through_conv(7, up2_adjoint(g_c2[..., :128]))
-        g = through_conv(6, g)                           # d / d p2
-        g = through_conv(5, pool2_adjoint(g) + g_c2[..., 128:])
-        g = through_conv(4, g)                           # d / d p1
-        g = through_conv(3, pool2_adjoint(g) + g_c1[..., 128:])
-        g = through_conv(2, g)                           # d / d p0
-        g = through_conv(1, pool2_adjoint(g) + g_c0[..., 64:])
-        through_conv(0, g)
+        gw = [conv3x3_weight_grad(a[inputs[i]], gz[i]) for i in range(len(L))]
+        gb = [gz[i].reshape(-1, gz[i].shape[3]).sum(axis=0) for i in range(len(L))]
         return loss, pack(list(zip(gw, gb)), (g_hw, g_hb))
+
+
+def round_bf16(x):
+    """x rounded to the nearest BF16 value (ties to even), returned as float64."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)

@@ -37,7 +37,7 @@ class Params(ctypes.Structure):
         ("lambda_s", ctypes.c_double), ("psi_b", ctypes.c_double), ("phi_b", ctypes.c_double),
         ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double), ("Gx", ctypes.c_double), ("Gy", ctypes.c_double),
         ("constraint", ctypes.c_int), ("multiplier", ctypes.c_int), ("precision", ctypes.c_int),
-        ("psi_on", ctypes.c_int),
+        ("psi_on", ctypes.c_int), ("wall_saturation", ctypes.c_int),
     ]
 
 
@@ -103,6 +103,38 @@ def _load():
     L.slbm_batch_last_error.restype = ctypes.c_char_p
     L.slbm_batch_destroy.argtypes = [vp]
     L.slbm_batch_destroy.restype = None
+    L.slbm_init_fields_device.argtypes = [vp, vp, vp]
+    L.slbm_batch_init_fields_device.argtypes = [vp, i, vp, vp]
+    # warm-start network and its conv primitives (include/surflbm_ws.h)
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.slbm_conv3x3_forward.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, vp]
+    L.slbm_conv3x3_flip_weights.argtypes = [vp, vp, i, i, vp]
+    L.slbm_conv3x3_input_grad.argtypes = [vp, vp, vp, vp, i, i, i, i, i, vp]
+    L.slbm_conv3x3_weight_grad.argtypes = [vp, vp, vp, i, i, i, i, i, vp]
+    L.slbm_conv_error.argtypes = [ctypes.POINTER(i)]
+    L.slbm_ws_create.argtypes = [i, i, i, ctypes.c_ulonglong, vp, ctypes.POINTER(vp)]
+    L.slbm_ws_param_count.argtypes = [vp]
+    L.slbm_ws_param_count.restype = ll
+    L.slbm_ws_get_params.argtypes = [vp, fp]
+    L.slbm_ws_set_params.argtypes = [vp, fp]
+    L.slbm_ws_forward.argtypes = [vp, vp, i, vp]
+    L.slbm_ws_loss_grad.argtypes = [vp, vp, vp, vp, i, dp, fp]
+    L.slbm_ws_adam.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    L.slbm_ws_train_step.argtypes = [vp, vp, vp, vp, i, ctypes.c_float, dp]
+    L.slbm_ws_batch_targets.argtypes = [vp, vp, i, d, vp]
+    L.slbm_ws_warm_start.argtypes = [vp, vp, ctypes.POINTER(i), fp, i, ctypes.POINTER(i)]
+    L.slbm_ws_device_bytes.argtypes = [vp]
+    L.slbm_ws_device_bytes.restype = ctypes.c_size_t
+    L.slbm_ws_last_error.argtypes = [vp]
+    L.slbm_ws_last_error.restype = ctypes.c_char_p
+    L.slbm_ws_destroy.argtypes = [vp]
+    L.slbm_ws_destroy.restype = None
+    for name in ("slbm_init_fields_device", "slbm_batch_init_fields_device", "slbm_conv3x3_forward",
+                 "slbm_conv3x3_flip_weights", "slbm_conv3x3_input_grad", "slbm_conv3x3_weight_grad",
+                 "slbm_conv_error", "slbm_ws_create", "slbm_ws_get_params", "slbm_ws_set_params",
+                 "slbm_ws_forward", "slbm_ws_loss_grad", "slbm_ws_adam", "slbm_ws_train_step",
+                 "slbm_ws_batch_targets", "slbm_ws_warm_start"):
+        getattr(L, name).restype = ctypes.c_int
     return L
 
 
@@ -298,6 +330,140 @@ class Batch:
     def close(self):
         if self._h:
             lib.slbm_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ---------------------------------------------------------------- warm start
+def _ptr(t):
+    """Device pointer of a torch tensor (or an int / None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _prim(st, what):
+    if st != SLBM_OK:
+        raise SlbmError(st, what)
+
+
+def conv3x3_forward(x, w, bias, y, relu=True, stream=None):
+    """y = act(conv3x3(x, w) + bias) on the tensor cores; x [B,H,W,Cin], w [Cout,3,3,Cin],
+    y [B,H,W,Cout] BF16 CUDA tensors, bias FP32 [Cout] or None."""
+    B, H, W, Cin = x.shape
+    _prim(lib.slbm_conv3x3_forward(_ptr(x), _ptr(w), _ptr(bias), _ptr(y), B, H, W, Cin, w.shape[0], int(relu),
+                                   _stream_handle(stream)), "conv3x3_forward")
+
+
+def conv3x3_flip_weights(w, wt, stream=None):
+    Cout, _, _, Cin = w.shape
+    _prim(lib.slbm_conv3x3_flip_weights(_ptr(w), _ptr(wt), Cin, Cout, _stream_handle(stream)), "flip_weights")
+
+
+def conv3x3_input_grad(dy, wt, mask, dx, stream=None):
+    """dx = (conv^T dy) * [mask > 0]; wt [Cin,3,3,Cout] from conv3x3_flip_weights."""
+    B, H, W, Cout = dy.shape
+    _prim(lib.slbm_conv3x3_input_grad(_ptr(dy), _ptr(wt), _ptr(mask), _ptr(dx), B, H, W, wt.shape[0], Cout,
+                                      _stream_handle(stream)), "conv3x3_input_grad")
+
+
+def conv3x3_weight_grad(x, dy, dw, stream=None):
+    """dw [Cout,3,3,Cin] (FP32) += d sum(dy * conv(x, w)) / dw."""
+    B, H, W, Cin = x.shape
+    _prim(lib.slbm_conv3x3_weight_grad(_ptr(x), _ptr(dy), _ptr(dw), B, H, W, Cin, dy.shape[3],
+                                       _stream_handle(stream)), "conv3x3_weight_grad")
+
+
+def conv_error():
+    """Synchronises; returns and clears the primitives' tensor-core timeout flag."""
+    f = ctypes.c_int()
+    _prim(lib.slbm_conv_error(ctypes.byref(f)), "conv_error")
+    return f.value
+
+
+class WarmStartNet:
+    """The warm-start encoder-decoder (see include/surflbm_ws.h)."""
+
+    def __init__(self, ny, nx, max_batch, seed=1, stream=None):
+        self.ny, self.nx, self.max_batch = ny, nx, max_batch
+        self._h = ctypes.c_void_p()
+        st = lib.slbm_ws_create(int(ny), int(nx), int(max_batch), int(seed), _stream_handle(stream),
+                                ctypes.byref(self._h))
+        if st != SLBM_OK:
+            raise SlbmError(st, lib.slbm_ws_last_error(None).decode())
+        self.nparam = lib.slbm_ws_param_count(self._h)
+
+    def _check(self, st):
+        if st != SLBM_OK:
+            raise SlbmError(st, lib.slbm_ws_last_error(self._h).decode())
+
+    def get_params(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        self._check(lib.slbm_ws_get_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        if flat.size != self.nparam:
+            raise ValueError("parameter count mismatch")
+        self._check(lib.slbm_ws_set_params(self._h, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def forward(self, cond, out):
+        """cond: CUDA float32 [B, 5]; out: CUDA float32 [B, 2, ny, nx]."""
+        self._check(lib.slbm_ws_forward(self._h, _ptr(cond), int(cond.shape[0]), _ptr(out)))
+
+    def loss_grad(self, cond, targets, idx=None, batch=None, want_grad=True):
+        """Loss (and host FP32 gradient) of rows idx (CUDA int32) or 0..batch-1."""
+        B = int(idx.shape[0]) if idx is not None else int(batch if batch is not None else cond.shape[0])
+        loss = ctypes.c_double()
+        g = np.empty(self.nparam, dtype=np.float32) if want_grad else None
+        self._check(lib.slbm_ws_loss_grad(self._h, _ptr(cond), _ptr(targets), _ptr(idx), B, ctypes.byref(loss),
+                                          g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if want_grad else None))
+        return loss.value, g
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(lib.slbm_ws_adam(self._h, lr, beta1, beta2, eps))
+
+    def train_step(self, cond, targets, idx, lr):
+        loss = ctypes.c_double()
+        self._check(lib.slbm_ws_train_step(self._h, _ptr(cond), _ptr(targets), _ptr(idx), int(idx.shape[0]),
+                                           float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def batch_targets(self, batch, idx, psi0, out):
+        """out (CUDA float32 [2, ny, nx]) = (phi, ln(psi/psi0)) of batch instance idx."""
+        self._check(lib.slbm_ws_batch_targets(self._h, batch._h, int(idx), float(psi0), _ptr(out)))
+
+    def warm_start(self, batch, which, cond):
+        """Replace the cold starts of batch instances `which` by projected predictions;
+        returns the accepted flags."""
+        which = np.ascontiguousarray(which, dtype=np.int32)
+        cond = np.ascontiguousarray(cond, dtype=np.float32)
+        acc = np.zeros(len(which), dtype=np.int32)
+        self._check(lib.slbm_ws_warm_start(self._h, batch._h, which.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                           cond.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), len(which),
+                                           acc.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return acc.astype(bool)
+
+    def device_bytes(self):
+        return lib.slbm_ws_device_bytes(self._h)
+
+    def close(self):
+        if self._h:
+            lib.slbm_ws_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

@@ -1,7 +1,8 @@
 """Builds the sm_103a shared library ``libsurflbm.so`` in-tree with nvcc.
 
 Usage: ``python -m paper_2609_26332_b300.build [--verbose]``.  The library holds
-the CUDA kernels and the C ABI declared in ``include/surflbm.h``.
+the CUDA kernels and the C ABI declared in ``include/surflbm.h`` and
+``include/surflbm_ws.h``.
 """
 import os
 import subprocess
@@ -11,8 +12,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libsurflbm.so")
-SOURCES = ["surflbm_api.cu", "surflbm_batch.cu"]
-HEADERS = ["surflbm_device.cuh", "surflbm_step.cuh", "surflbm_internal.cuh"]
+SOURCES = ["surflbm_api.cu", "surflbm_batch.cu", "ws_net.cu"]
+HEADERS = ["surflbm_device.cuh", "surflbm_step.cuh", "surflbm_internal.cuh", "ws_tc.cuh", "ws_conv.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -27,7 +28,7 @@ def needs_build():
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "surflbm.h")]
+    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", h) for h in ("surflbm.h", "surflbm_ws.h")]
     return any(os.path.getmtime(p) > t for p in deps)
 
 

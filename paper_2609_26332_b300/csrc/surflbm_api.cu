@@ -107,6 +107,7 @@ std::string validate(const slbm_params* p) {
     if (p->constraint != SLBM_CONSTRAINT_NONLINEAR && p->constraint != SLBM_CONSTRAINT_LINEAR) return "bad constraint";
     if (p->multiplier != SLBM_MULT_PAPER && p->multiplier != SLBM_MULT_TARGET) return "bad multiplier";
     if (p->precision < SLBM_FP32 || p->precision > SLBM_BF16DEV) return "bad precision";
+    if (p->wall_saturation != 0 && p->wall_saturation != 1) return "wall_saturation must be 0 or 1";
     return "";
 }
 
@@ -115,8 +116,13 @@ void set_wall_phys(slbm_domain* d, int w) {
     const double sg = d->p.sigma * (16.0 / 15.0 + c) / 2.0;
     const double sl = d->p.sigma * (16.0 / 15.0 - c) / 2.0;
     d->phys.wcos[w] = (float)(d->p.sigma * c);
-    d->phys.wA[w] = (float)(sg * d->wall_bsg[w] - sl * d->wall_bsl[w]);
-    d->phys.wB[w] = (float)(sg * d->wall_bsg[w] + sl * d->wall_bsl[w]);
+    d->phys.wSg[w] = (float)(sg * d->wall_bsg[w]);
+    d->phys.wSl[w] = (float)(sl * d->wall_bsl[w]);
+    d->phys.wS0g[w] = (float)sg;
+    d->phys.wS0l[w] = (float)sl;
+    const bool sat = d->p.wall_saturation != 0;
+    d->phys.wLg[w] = (sat && d->wall_bsg[w] > 0.0) ? (float)(-0.5 / d->wall_bsg[w]) : -1e30f;
+    d->phys.wLl[w] = (sat && d->wall_bsl[w] > 0.0) ? (float)(-0.5 / d->wall_bsl[w]) : -1e30f;
     d->phys.uw[w] = (float)d->wall_u[w];
 }
 
@@ -348,6 +354,7 @@ void slbm_default_params(slbm_params* p, int nx, int ny) {
     p->rho_l = 1.0; p->rho_g = 1.0;
     p->constraint = SLBM_CONSTRAINT_NONLINEAR; p->multiplier = SLBM_MULT_PAPER;
     p->precision = SLBM_FP32; p->psi_on = 1;
+    p->wall_saturation = 1;
 }
 
 slbm_status slbm_create_domain(const slbm_params* p, void* stream, slbm_domain** out) {
@@ -417,7 +424,8 @@ slbm_status slbm_set_walls(slbm_domain* d, int wall, double theta0_deg, double b
     return SLBM_OK;
 }
 
-slbm_status slbm_init_fields(slbm_domain* d, const double* phi, const double* psi) {
+namespace {
+slbm_status init_fields_from(slbm_domain* d, const double* phi, const double* psi, cudaMemcpyKind kind) {
     if (!d || !phi) return d ? fail(d, SLBM_EINVAL, "phi is NULL") : SLBM_EINVAL;
     if (d->p.psi_on && !psi) return fail(d, SLBM_EINVAL, "psi is NULL while psi_on = 1");
     const size_t bytes = (size_t)d->N * sizeof(double);
@@ -425,9 +433,10 @@ slbm_status slbm_init_fields(slbm_domain* d, const double* phi, const double* ps
         slbm_status s = dalloc(d, &d->fields, 5 * bytes);
         if (s) return s;
     }
-    cudaError_t e = cudaMemcpyAsync(d->fields, phi, bytes, cudaMemcpyHostToDevice, d->stream);
-    if (e == cudaSuccess && d->p.psi_on)
-        e = cudaMemcpyAsync(d->fields + d->N, psi, bytes, cudaMemcpyHostToDevice, d->stream);
+    cudaError_t e = cudaSuccess;
+    if (phi != d->fields) e = cudaMemcpyAsync(d->fields, phi, bytes, kind, d->stream);
+    if (e == cudaSuccess && d->p.psi_on && psi != d->fields + d->N)
+        e = cudaMemcpyAsync(d->fields + d->N, psi, bytes, kind, d->stream);
     if (e != cudaSuccess) return cuda_fail(d, e, "cudaMemcpyAsync (init)");
     d->cur = 0;
     d->n = 0;
@@ -442,6 +451,15 @@ slbm_status slbm_init_fields(slbm_domain* d, const double* phi, const double* ps
     if (e != cudaSuccess) return cuda_fail(d, e, "init");
     d->initialised = true;
     return SLBM_OK;
+}
+}  // namespace
+
+slbm_status slbm_init_fields(slbm_domain* d, const double* phi, const double* psi) {
+    return init_fields_from(d, phi, psi, cudaMemcpyHostToDevice);
+}
+
+slbm_status slbm_init_fields_device(slbm_domain* d, const double* phi, const double* psi) {
+    return init_fields_from(d, phi, psi, cudaMemcpyDeviceToDevice);
 }
 
 slbm_status slbm_step(slbm_domain* d, long long nsteps) {

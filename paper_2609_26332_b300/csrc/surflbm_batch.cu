@@ -69,37 +69,6 @@ cudaError_t prepare_batch_kernels() {
 
 }  // namespace
 
-struct slbm_batch {
-    int count = 0;
-    int precision = 0;
-    bool var = false;                 // some instance has variable density / viscosity
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    std::vector<slbm_domain*> dom;
-    std::vector<char> active;
-    std::vector<long long> G0;        // batch step at each instance's time level 0
-    long long G = 0;                  // host mirror of the device step counter
-    int band_rows = 64, ctas_per_sm = 2, graph_steps = 32;
-    // device tables
-    InstDesc* d_inst = nullptr;
-    Piece* d_pieces = nullptr;
-    double* d_partials = nullptr;     // per instance: max pieces * NPART
-    unsigned int* d_counters = nullptr;  // per instance
-    unsigned int* d_queue = nullptr;  // [0]: queue, [1]: done
-    long long* d_G = nullptr;
-    std::vector<size_t> part_off;     // offset of each instance's partial slots (doubles)
-    std::vector<int> max_pieces;
-    int npieces = 0, nctas = 1;
-    bool tables_valid = false;
-    cudaGraphExec_t graph = nullptr;
-    int graph_len = 0;
-    // residual
-    float* d_snap_base = nullptr;
-    std::vector<size_t> snap_off;
-    bool have_snap = false;
-    std::string err = "no error";
-    size_t bytes = 0;
-};
 
 namespace {
 
@@ -320,7 +289,10 @@ slbm_status residuals(slbm_batch* b, long long K, std::vector<double>& r) {
         for (size_t k = 0; k < args.size(); ++k) {
             const double rp = std::sqrt(h[4 * k]) / ((double)K * std::sqrt(std::max(h[4 * k + 1], 1e-300)));
             const double rs = std::sqrt(h[4 * k + 2]) / ((double)K * std::sqrt(std::max(h[4 * k + 3], 1e-300)));
-            r[which[k]] = b->dom[which[k]]->p.psi_on ? std::max(rp, rs) : rp;
+            const bool psi_on = b->dom[which[k]]->p.psi_on;
+            const bool finite = std::isfinite(h[4 * k]) && std::isfinite(h[4 * k + 1]) &&
+                                (!psi_on || (std::isfinite(h[4 * k + 2]) && std::isfinite(h[4 * k + 3])));
+            r[which[k]] = !finite ? NAN : psi_on ? std::max(rp, rs) : rp;
         }
     }
     b->have_snap = true;
@@ -438,6 +410,18 @@ slbm_status slbm_batch_init_fields(slbm_batch* b, int idx, const double* phi, co
     return SLBM_OK;
 }
 
+slbm_status slbm_batch_init_fields_device(slbm_batch* b, int idx, const double* phi, const double* psi) {
+    if (!b) return SLBM_EINVAL;
+    if (idx < 0 || idx >= b->count) return bfail(b, SLBM_EINVAL, "instance index out of range");
+    slbm_status s = slbm_init_fields_device(b->dom[idx], phi, psi);
+    if (s) return bfail(b, s, b->dom[idx]->err);
+    b->active[idx] = 1;
+    b->G0[idx] = b->G;
+    b->tables_valid = false;
+    b->have_snap = false;
+    return SLBM_OK;
+}
+
 slbm_status slbm_batch_set_tiling(slbm_batch* b, int band_rows, int ctas_per_sm, int graph_steps) {
     if (!b) return SLBM_EINVAL;
     if (band_rows < 8 || ctas_per_sm < 1 || ctas_per_sm > 2 || graph_steps < 1)
@@ -476,8 +460,9 @@ slbm_status slbm_batch_run_to_equilibrium(slbm_batch* b, double tol, long long m
         if (s) return s;
         bool changed = false;
         for (int i = 0; i < b->count; ++i) {
-            if (b->active[i] && r[i] < tol) {
-                steps_out[i] = b->dom[i]->n;
+            if (!b->active[i]) continue;
+            if (r[i] < tol || std::isnan(r[i])) {
+                steps_out[i] = std::isnan(r[i]) ? -2 : b->dom[i]->n;   // NaN residual: diverged
                 b->active[i] = 0;
                 changed = true;
             }

@@ -2,6 +2,7 @@
 // batch (whose instances are domains stepped by the batch kernel).
 #pragma once
 #include <string>
+#include <vector>
 #include "surflbm.h"
 #include "surflbm_step.cuh"
 
@@ -30,4 +31,37 @@ struct slbm_domain {
     double* fields = nullptr;   // 5 N doubles, allocated on first read
     size_t bytes = 0;
     std::string err = "no error";
+};
+
+// A batch of domains stepped by the tile-queue kernel (surflbm_batch.cu).
+struct slbm_batch {
+    int count = 0;
+    int precision = 0;
+    bool var = false;                 // some instance has variable density / viscosity
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<slbm_domain*> dom;
+    std::vector<char> active;
+    std::vector<long long> G0;        // batch step at each instance's time level 0
+    long long G = 0;                  // host mirror of the device step counter
+    int band_rows = 64, ctas_per_sm = 2, graph_steps = 32;
+    // device tables
+    slbm::InstDesc* d_inst = nullptr;
+    slbm::Piece* d_pieces = nullptr;
+    double* d_partials = nullptr;     // per instance: max pieces * NPART
+    unsigned int* d_counters = nullptr;  // per instance
+    unsigned int* d_queue = nullptr;  // [0]: queue, [1]: done
+    long long* d_G = nullptr;
+    std::vector<size_t> part_off;     // offset of each instance's partial slots (doubles)
+    std::vector<int> max_pieces;
+    int npieces = 0, nctas = 1;
+    bool tables_valid = false;
+    cudaGraphExec_t graph = nullptr;
+    int graph_len = 0;
+    // residual
+    float* d_snap_base = nullptr;
+    std::vector<size_t> snap_off;
+    bool have_snap = false;
+    std::string err = "no error";
+    size_t bytes = 0;
 };

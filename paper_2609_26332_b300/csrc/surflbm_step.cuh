@@ -63,7 +63,10 @@ struct Phys {
     float sf[5], sg[5], sh[5];   // (s0, s1, s2, s3, s4) per set; s2 of the flow set = 1/tau_f
     int mrt_f, mrt_g, mrt_h;      // 0: all rates equal (BGK path)
     int var_nu;                   // nu_l != nu_g
-    float wcos[2], wA[2], wB[2], uw[2];
+    float wcos[2], uw[2];
+    // per wall: sigma_sg,0 beta_sg, sigma_sl,0 beta_sl, sigma_sg,0, sigma_sl,0 and the
+    // ln(1 - psi) below which each tension sits on its Remark-1 cap (-1e30: never)
+    float wSg[2], wSl[2], wS0g[2], wS0l[2], wLg[2], wLl[2];
     float psi_clamp;
     int psi_on, linear, target;
     double Nd;                    // number of cells
@@ -166,8 +169,14 @@ __device__ __forceinline__ void wall_ghost(float ph, float ps, int w, const Phys
     float u = ph * P.inv_phi_b;
     float gp = 0.75f * P.inv_phi_b * (1.0f - u * u);
     float gv = 0.75f * u - 0.25f * u * u * u;
-    float dfdphi = -(P.wcos[w] + L * P.wA[w]) * gp;
-    float dfdpsi = (P.wA[w] * gv - 0.5f * P.wB[w]) / (1.0f - psc);
+    // f_w = (1/2 - g) sigma_sg + (1/2 + g) sigma_sl, sigma_s,a = sigma_s,a,0 (1 + beta_a L)
+    // (Eq. langmuir) or sigma_s,a,0 / 2 on the cap (Remark 1)
+    const bool on_sg = L > P.wLg[w], on_sl = L > P.wLl[w];
+    const float st_sg = on_sg ? P.wSg[w] * L : -0.5f * P.wS0g[w];
+    const float st_sl = on_sl ? P.wSl[w] * L : -0.5f * P.wS0l[w];
+    float dfdphi = -(P.wcos[w] + st_sg - st_sl) * gp;
+    float dfdpsi = -((0.5f - gv) * (on_sg ? P.wSg[w] : 0.0f) + (0.5f + gv) * (on_sl ? P.wSl[w] : 0.0f)) /
+                   (1.0f - psc);
     phG = P.kappa > 0.0f ? ph - dfdphi / P.kappa : ph;
     psG = (P.lambda_s > 0.0f && P.psi_on) ? ps - dfdpsi / P.lambda_s : ps;
 }

@@ -48,3 +48,19 @@ def test_default_params_and_validation():
     assert B.lib.slbm_step(None, 1) == B.SLBM_EINVAL
     assert B.lib.slbm_set_walls(None, 0, 90.0, 0.0, 0.0, 0.0) == B.SLBM_EINVAL
     B.lib.slbm_destroy(None)
+
+
+def test_warm_start_entry_points_validate_before_touching_the_gpu():
+    import ctypes
+    from paper_2609_26332_b300 import binding as B
+    h = ctypes.c_void_p()
+    for ny, nx, mb in ((12, 32, 1), (16, 30, 1), (16, 32, 0)):
+        assert B.lib.slbm_ws_create(ny, nx, mb, 1, None, ctypes.byref(h)) == B.SLBM_EINVAL
+    # channel counts the tensor-core tiles cannot take
+    assert B.lib.slbm_conv3x3_forward(None, None, None, None, 1, 8, 8, 16, 32, 1, None) == B.SLBM_EINVAL
+    fake = ctypes.c_void_p(1 << 20)
+    assert B.lib.slbm_conv3x3_forward(fake, fake, None, fake, 1, 8, 8, 12, 32, 1, None) == B.SLBM_EINVAL
+    assert B.lib.slbm_conv3x3_forward(fake, fake, None, fake, 1, 8, 8, 16, 40, 1, None) == B.SLBM_EINVAL
+    assert B.lib.slbm_conv3x3_input_grad(fake, fake, None, fake, 1, 8, 8, 24, 32, None) == B.SLBM_EINVAL
+    assert B.lib.slbm_conv3x3_weight_grad(fake, fake, fake, 1, 8, 8, 32, 256, None) == B.SLBM_EINVAL
+    assert B.lib.slbm_ws_param_count(None) == 0

@@ -1,0 +1,217 @@
+"""Warm-start network on the GPU: the tcgen05 convolution kernels (forward, input
+gradient, weight gradient) and the whole-network loss and gradient against the FP64
+oracle on the same BF16-rounded inputs.
+
+Tolerances follow from the arithmetic: operands are BF16 (exact products in FP32),
+accumulation is FP32 over K = 9 Cin (or the pixel count) terms, and BF16 outputs are
+rounded to 8 significant bits (relative error <= 2^-9).  Through the 14 layers of the
+network every activation and gradient is rounded to BF16 again, so the whole-network
+comparison is in relative L2 norm per tensor."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import warmstart as ows
+
+
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _bf(torch, a):
+    return torch.tensor(np.asarray(a, dtype=np.float32), dtype=torch.bfloat16, device="cuda")
+
+
+def _f64(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+CONV_CASES = [
+    # B, H, W, Cin, Cout: ragged pixel counts (not multiples of 128), every channel count of the network
+    (1, 10, 13, 16, 32),
+    (2, 16, 32, 32, 64),
+    (1, 8, 24, 96, 32),
+    (2, 9, 16, 256, 128),
+    (1, 12, 20, 192, 64),
+    (1, 4, 40, 128, 128),
+    (3, 7, 11, 64, 64),
+]
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout", CONV_CASES)
+def test_conv_forward_matches_oracle(B, H, W, Cin, Cout):
+    torch = _cuda()
+    from paper_2609_26332_b300 import binding as Bd
+    rng = np.random.default_rng(Cin * 1000 + Cout)
+    x = _bf(torch, rng.standard_normal((B, H, W, Cin)))
+    w = _bf(torch, rng.uniform(-1, 1, (Cout, 3, 3, Cin)) * np.sqrt(3.0 / (9 * Cin)))
+    b = torch.tensor(rng.uniform(-0.2, 0.2, Cout), dtype=torch.float32, device="cuda")
+    y = torch.empty((B, H, W, Cout), dtype=torch.bfloat16, device="cuda")
+    for relu in (False, True):
+        Bd.conv3x3_forward(x, w, b, y, relu=relu)
+        assert Bd.conv_error() == 0
+        ref = ows.conv3x3(_f64(x), _f64(w), b.cpu().numpy().astype(np.float64))
+        if relu:
+            ref = np.maximum(ref, 0.0)
+        got = _f64(y)
+        err = np.abs(got - ref)
+        tol = 2.0 ** -8 * np.abs(ref) + 1e-3 * np.sqrt(np.mean(ref ** 2))
+        assert (err <= tol).all(), (relu, err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout", [c for c in CONV_CASES if c[3] % 16 == 0])
+def test_conv_input_grad_matches_oracle(B, H, W, Cin, Cout):
+    torch = _cuda()
+    from paper_2609_26332_b300 import binding as Bd
+    rng = np.random.default_rng(7 + Cin + Cout)
+    dy = _bf(torch, rng.standard_normal((B, H, W, Cout)))
+    w = _bf(torch, rng.uniform(-1, 1, (Cout, 3, 3, Cin)) * np.sqrt(3.0 / (9 * Cout)))
+    mask = _bf(torch, rng.standard_normal((B, H, W, Cin)))
+    wt = torch.empty((Cin, 3, 3, Cout), dtype=torch.bfloat16, device="cuda")
+    Bd.conv3x3_flip_weights(w, wt)
+    # the flipped layout itself
+    assert torch.equal(wt.cpu(), w.cpu().permute(3, 1, 2, 0).flip(1, 2))
+    dx = torch.empty((B, H, W, Cin), dtype=torch.bfloat16, device="cuda")
+    for m in (None, mask):
+        Bd.conv3x3_input_grad(dy, wt, m, dx)
+        assert Bd.conv_error() == 0
+        ref = ows.conv3x3_input_grad(_f64(dy), _f64(w))
+        if m is not None:
+            ref = ref * (_f64(mask) > 0)
+        err = np.abs(_f64(dx) - ref)
+        tol = 2.0 ** -8 * np.abs(ref) + 1e-3 * np.sqrt(np.mean(ref ** 2))
+        assert (err <= tol).all(), (m is None, err.max())
+
+
+WG_CASES = [c for c in CONV_CASES if c[3] % 16 == 0 and c[4] <= 128] + [(3, 40, 48, 32, 64), (2, 64, 128, 16, 32)]
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout", WG_CASES)
+def test_conv_weight_grad_matches_oracle(B, H, W, Cin, Cout):
+    torch = _cuda()
+    from paper_2609_26332_b300 import binding as Bd
+    rng = np.random.default_rng(11 + Cin + 3 * Cout)
+    x = _bf(torch, rng.standard_normal((B, H, W, Cin)))
+    dy = _bf(torch, rng.standard_normal((B, H, W, Cout)))
+    dw = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device="cuda")
+    Bd.conv3x3_weight_grad(x, dy, dw)
+    assert Bd.conv_error() == 0
+    ref = ows.conv3x3_weight_grad(_f64(x), _f64(dy))
+    err = np.abs(dw.cpu().numpy().astype(np.float64) - ref)
+    assert err.max() <= 1e-4 * np.abs(ref).max() + 1e-5, err.max()
+    # accumulation: a second call adds the same gradient
+    Bd.conv3x3_weight_grad(x, dy, dw)
+    assert np.abs(dw.cpu().numpy() - 2 * ref).max() <= 2e-4 * np.abs(ref).max() + 1e-5
+
+
+def _problem(seed, H, W, B):
+    rng = np.random.default_rng(seed)
+    cond = np.stack([rng.uniform([30, 0, 0, 0.005, 0.05], [150, 1, 1, 0.05, 0.09]) for _ in range(B)])
+    targets = np.stack([np.stack([np.tanh(rng.standard_normal((H, W))), 0.3 * rng.standard_normal((H, W))])
+                        for _ in range(B)])
+    return cond, targets
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_network_forward_loss_and_gradient_match_oracle():
+    """Whole network: forward outputs, loss and every parameter gradient against the
+    oracle run with the same BF16 rounding points (round_bf16 wherever the GPU stores a
+    BF16 tensor).  Each conv kernel alone gives the BF16-rounded oracle value in 99.9 %
+    of its outputs (FP32 vs FP64 accumulation flips the rest by one BF16 step); through
+    the 14 layers those flips spread, and in a measured run the fraction of bit-equal
+    activations falls from 0.9999 in the encoder to 0.94 at the last conv, the output
+    differing by 3e-3 to 1e-2 in relative L2.  The bounds below sit above that spread
+    and far below what a wrong term (a dropped skip gradient, a missing mask: O(1)
+    errors in the layers it feeds) would give.  The exact-FP64 oracle is compared too."""
+    torch = _cuda()
+    from paper_2609_26332_b300 import binding as Bd
+    H, W, B = 16, 32, 2
+    net = Bd.WarmStartNet(H, W, max_batch=4, seed=3)
+    flat = net.get_params().astype(np.float64)
+    # the oracle sees the conv weights as the GPU does (BF16), biases and head in FP32
+    layers, head = ows.unpack(flat)
+    layers = [(ows.round_bf16(w), b) for w, b in layers]
+    onet = ows.Net(ows.pack(layers, head))
+    cond, targets = _problem(5, H, W, B)
+    cond_t = torch.tensor(cond, dtype=torch.float32, device="cuda")
+    tgt_t = torch.tensor(targets, dtype=torch.float32, device="cuda")
+    out = torch.empty((B, 2, H, W), dtype=torch.float32, device="cuda")
+    net.forward(cond_t, out)
+    loss, grad = net.loss_grad(cond_t, tgt_t)
+    q = ows.round_bf16
+    cond32 = cond.astype(np.float32).astype(np.float64)
+    ref_out, _ = onet.forward(cond32, H, W, q)
+    ref_loss, ref_grad = onet.loss_grad(cond32, targets.astype(np.float32), q)
+    ex_out, _ = onet.forward(cond32, H, W)
+    ex_loss, ex_grad = onet.loss_grad(cond32, targets.astype(np.float32))
+    r_out, r_ex = _rel(out.cpu().numpy(), ref_out), _rel(out.cpu().numpy(), ex_out)
+    print(f"forward rel L2 {r_out:.2e} (exact oracle {r_ex:.2e}); loss {loss:.8e} vs {ref_loss:.8e} "
+          f"(exact {ex_loss:.8e})")
+    assert r_out < 3e-2 and r_ex < 3e-2
+    assert abs(loss - ref_loss) <= 2e-3 * ref_loss
+    gl, (ghw, ghb) = ows.unpack(grad.astype(np.float64))
+    rl, (rhw, rhb) = ows.unpack(ref_grad)
+    el, _ = ows.unpack(ex_grad)
+    for i, ((gw, gb), (rw, rb), (xw, _)) in enumerate(zip(gl, rl, el)):
+        ew, eb, ex = _rel(gw, rw), _rel(gb, rb), _rel(gw, xw)
+        print(f"conv {i}: weight grad rel L2 {ew:.2e}, bias grad {eb:.2e} (exact oracle {ex:.2e})")
+        assert ew < 6e-2 and eb < 6e-2, i
+        assert ex < 1.5e-1, i
+    assert _rel(ghw, rhw) < 2e-2 and _rel(ghb, rhb) < 2e-2
+
+
+def test_training_reduces_the_loss():
+    torch = _cuda()
+    from paper_2609_26332_b300 import binding as Bd
+    H, W, S = 16, 32, 16
+    net = Bd.WarmStartNet(H, W, max_batch=8, seed=9)
+    rng = np.random.default_rng(2)
+    cond = np.stack([rng.uniform([30, 0, 0, 0.005, 0.05], [150, 1, 1, 0.05, 0.09]) for _ in range(S)])
+    # a smooth target that depends on the parameters: a tanh cap of height set by theta0
+    yy, xx = np.meshgrid(np.arange(H) + 0.5, np.arange(W) + 0.5 - W / 2, indexing="ij")
+    tg = np.stack([np.stack([np.tanh((6 + 4 * (c[0] - 90) / 60 - np.hypot(xx, yy)) / 2), 0.5 * c[1] + 0 * xx])
+                   for c in cond])
+    cond_t = torch.tensor(cond, dtype=torch.float32, device="cuda")
+    tgt_t = torch.tensor(tg, dtype=torch.float32, device="cuda")
+    first = None
+    for it in range(150):
+        idx = torch.tensor(rng.choice(S, 8, replace=False), dtype=torch.int32, device="cuda")
+        loss = net.train_step(cond_t, tgt_t, idx, lr=2e-3)
+        first = loss if first is None else first
+    full, _ = net.loss_grad(cond_t, tgt_t, idx=torch.arange(8, dtype=torch.int32, device="cuda"), want_grad=False)
+    print(f"loss {first:.4e} -> {full:.4e}")
+    assert full < 0.1 * first
+
+
+def test_warm_start_keeps_the_cold_start_totals():
+    """The projected prediction replaces the cold start with the same sum psi and the
+    same H = sum h_phi(phi) (the two conserved totals of the method), also for an
+    untrained network whose raw prediction is far from either."""
+    torch = _cuda()
+    from paper_2609_26332_b300 import binding as Bd, warmstart as WS
+    specs = WS.drop_specs(3, seed=5, ny=32, nx=64)
+    net = Bd.WarmStartNet(32, 64, max_batch=2, seed=4)     # two forward chunks for three drops
+    cold = WS.cold_batch(specs)
+    warm = WS.cold_batch(specs)
+    acc = net.warm_start(warm, [0, 1, 2], WS.cond_rows(specs))
+    assert acc.all()
+    for i in range(3):
+        tc, tw = cold.read_totals(i), warm.read_totals(i)
+        assert tw["step"] == 0
+        assert abs(tw["psi_total"] - tc["psi_total"]) <= 1e-9 * tc["psi_total"]
+        assert abs(tw["H"] - tc["H"]) <= 1e-6 * 64 * 32
+        fw, fc = warm.read_fields(i), cold.read_fields(i)
+        assert np.abs(fw["phi"] - fc["phi"]).max() > 1e-2          # the state did change
+        assert np.all(fw["psi"] > 0)
+    # the warm-started batch steps like any other
+    warm.step(20)
+    assert all(warm.read_totals(i)["range_count"] == 0 for i in range(3))
+    cold.close()
+    warm.close()

@@ -97,3 +97,13 @@ def test_finite_differences_catch_a_planted_adjoint_error(monkeypatch):
     fd = (ws.Net(fp).loss(cond, targets) - ws.Net(fm).loss(cond, targets)) / (2 * h)
     assert abs(fd) > 1e-8
     assert abs(fd - bad[i]) > 1e-3 * abs(fd)
+
+
+def test_round_bf16_matches_torch_conversion():
+    import torch
+    rng = np.random.default_rng(8)
+    x = np.concatenate([rng.standard_normal(5000) * 10.0 ** rng.integers(-8, 8, 5000),
+                        # exact ties between two BF16 values (odd and even last kept bit)
+                        np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(2.0 + 2.0 ** -7), 0.0])])
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(ws.round_bf16(x), ref)

@@ -36,3 +36,60 @@ def test_solid_adsorption_trends():
         ang[name], _ = contact_angle(o.fields()["phi"], 4.0)
     assert ang["sl"] < ang["none"] - 1.0
     assert ang["sg"] > ang["none"] + 1.0
+
+
+def _strong_adsorption_oracle(saturation, nx=48, ny=24):
+    p = OracleParams(nx=nx, ny=ny, psi_b=0.04, multiplier="target", saturation=saturation,
+                     walls=[Wall(92.0, 0.98, 0.98, 0.0), Wall(90.0)])
+    phi0, psi0 = inputs.sessile_drop(nx, ny, 7.0, 4.0, phi_b=inputs.bulk_phi(0.04, 1.0), psi0=0.04)
+    return Oracle(p, phi0, psi0)
+
+
+def test_saturation_cap_is_the_remark_1_tension_law():
+    """Remark 1: sigma_s,a(psi) = sigma_s,a,0 max(1/2, 1 + beta_a ln(1 - psi)).  The wall
+    energy built from the capped tensions is continuous at the cap, its psi-derivative
+    used by the closure matches a centred difference of it off the cap and vanishes on
+    it for that tension, and below the cap nothing changes."""
+    o = _strong_adsorption_oracle(True)
+    d, p = o.d, o.p
+    g = 0.3      # a value of g(phi) in the interface
+    def fw(psi):
+        L = np.log1p(-psi)
+        t_sg, t_sl, _, _ = o._wall_tension_factors(0, np.array([L]))
+        sg = d.wall_sg0[0] * (1 + t_sg[0])
+        sl = d.wall_sl0[0] * (1 + t_sl[0])
+        ref_sg = d.wall_sg0[0] * max(0.5, 1 + 0.98 * L)
+        ref_sl = d.wall_sl0[0] * max(0.5, 1 + 0.98 * L)
+        assert np.isclose(sg, ref_sg, rtol=1e-14) and np.isclose(sl, ref_sl, rtol=1e-14)
+        return (0.5 - g) * sg + (0.5 + g) * sl
+    kink = 1.0 - np.exp(-0.5 / 0.98)
+    assert abs(fw(kink - 1e-9) - fw(kink + 1e-9)) < 1e-10
+    for psi in (0.05, 0.2, kink - 0.01, kink + 0.05):
+        L = np.log1p(-psi)
+        _, _, on_sg, on_sl = o._wall_tension_factors(0, np.array([L]))
+        dfdpsi = -((0.5 - g) * d.wall_sg0[0] * 0.98 * on_sg[0] + (0.5 + g) * d.wall_sl0[0] * 0.98 * on_sl[0]) / (1 - psi)
+        h = 1e-7
+        assert np.isclose(dfdpsi, (fw(psi + h) - fw(psi - h)) / (2 * h), rtol=1e-5, atol=1e-12)
+    # below the cap the closure is the plain logarithmic law
+    a, b = _strong_adsorption_oracle(True), _strong_adsorption_oracle(False)
+    a.step(5)
+    b.step(5)
+    assert np.abs(a.fields()["psi"][0]).max() < kink
+    assert np.allclose(a.fields()["psi"], b.fields()["psi"], rtol=0, atol=1e-14)
+
+
+def test_saturation_cap_keeps_a_strongly_adsorbing_wall_bounded():
+    """beta_sg = beta_sl = 0.98 with psi0 = 0.04: with the plain logarithmic law the wall
+    surfactant runs to the psi = 1 singularity (no bounded equilibrium); with the cap of
+    Remark 1 it levels off near the cap value 1 - exp(-1/(2 beta)) = 0.40."""
+    kink = 1.0 - np.exp(-0.5 / 0.98)
+    a = _strong_adsorption_oracle(True)
+    a.step(1500)
+    wall = a.fields()["psi"][0]
+    assert np.isfinite(a.fields()["phi"]).all()
+    assert wall.max() < kink + 0.05
+    b = _strong_adsorption_oracle(False)
+    with np.errstate(all="ignore"):
+        b.step(600)
+    wb = b.fields()["psi"][0]
+    assert not np.isfinite(wb).all() or wb.max() > kink + 0.15
