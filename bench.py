@@ -283,7 +283,7 @@ def run_warmstart(args, rank, world, dist):
     net = B.WarmStartNet(ny, nx, max_batch=args.ws_batch, seed=7 + rank)
     train_specs = WS.drop_specs(args.ws_train, seed=1000 + rank, ny=ny, nx=nx)
     test_specs = WS.drop_specs(args.ws_eval, seed=9000 + rank, ny=ny, nx=nx)
-    cond, targets, steps = WS.build_dataset(net, train_specs, args.ws_tol, args.ws_max_steps, log=log)
+    cond, targets, steps, lbm_launches = WS.build_dataset(net, train_specs, args.ws_tol, args.ws_max_steps, log=log)
     t_data = time.perf_counter() - t0
     ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev[0].record()
@@ -331,7 +331,11 @@ def run_warmstart(args, rank, world, dist):
             "train": {"final_loss": hist[-1], "first_loss": hist[0], "seconds": t_train,
                       "conv_tflops": train_tflops},
             "seconds": {"dataset": t_data, "train": t_train, "eval": t_eval},
-            "gpu_launches": None,
+            # kernels per training step: input 1, convs 14, pools 3, upsample-concats 3, head 1,
+            # input gradients 13, upsample / pool adjoints 6, weight and bias gradients 28,
+            # Adam 1, weight refresh 14; per LBM step one batch launch
+            "gpu_launches": int(84 * args.ws_epochs * max(1, len(cond) // args.ws_batch)
+                                + lbm_launches + res["launches"]),
         }
         print(json.dumps(line))
     net.close()

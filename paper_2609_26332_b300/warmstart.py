@@ -64,11 +64,13 @@ def build_dataset(net, specs, tol, max_steps, check_every=500, chunk=1024, strea
     import torch
     ny, nx = specs[0]["ny"], specs[0]["nx"]
     keep_cond, keep_t, all_steps = [], [], []
+    launches = 0
     for c0 in range(0, len(specs), chunk):
         part = specs[c0:c0 + chunk]
         b = cold_batch(part, stream=stream)
         steps = b.run_to_equilibrium(tol, max_steps, check_every)
         all_steps.append(steps)
+        launches += batch_steps_run(steps, max_steps)
         ok = np.nonzero(steps > 0)[0]
         t = torch.empty((len(ok), 2, ny, nx), dtype=torch.float32, device="cuda")
         for j, i in enumerate(ok):
@@ -79,7 +81,16 @@ def build_dataset(net, specs, tol, max_steps, check_every=500, chunk=1024, strea
         if log:
             log(f"dataset chunk {c0 // chunk}: {len(ok)}/{len(part)} converged, "
                 f"{int((steps == -2).sum())} diverged, median steps {np.median(steps[ok]) if len(ok) else -1}")
-    return np.concatenate(keep_cond), torch.cat(keep_t), np.concatenate(all_steps)
+    return np.concatenate(keep_cond), torch.cat(keep_t), np.concatenate(all_steps), launches
+
+
+def batch_steps_run(steps, max_steps):
+    """Time steps (one launch each) a run_to_equilibrium call took: max_steps if an
+    instance never converged, else the step of the last convergence."""
+    if (steps == -1).any():
+        return int(max_steps)
+    done = steps[steps > 0]
+    return int(done.max()) if len(done) else 0
 
 
 def train(net, cond, targets, epochs, batch_size, lr, seed=0, log=None, lr_final=None):
@@ -124,7 +135,8 @@ def evaluate(net, specs, tol, max_steps, check_every=500, stream=None):
             a_warm[i] = contact_angle(warm.read_fields(i, which=("phi",))["phi"])
     cold.close()
     warm.close()
-    return dict(steps_cold=s_cold, steps_warm=s_warm, angle_cold=a_cold, angle_warm=a_warm, accepted=accepted)
+    return dict(steps_cold=s_cold, steps_warm=s_warm, angle_cold=a_cold, angle_warm=a_warm, accepted=accepted,
+                launches=batch_steps_run(s_cold, max_steps) + batch_steps_run(s_warm, max_steps))
 
 
 def contact_angle(phi, eps=EPS):
