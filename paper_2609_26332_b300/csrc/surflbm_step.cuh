@@ -396,18 +396,23 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
                 const int y = r0 + rr;
                 if (y < 0 || y >= ny) continue;
                 unsigned char* row = base + (size_t)rr * ST::ROW;
-                const long long rowoff = (long long)y * nx + ws;
+                const long long rowoff = (long long)y * nx;
+                // a 16-byte chunk never straddles the periodic seam (window start and nx are
+                // multiples of the elements per chunk), so each chunk is fetched from its
+                // wrapped column
                 if (q < 16 * CD) {
                     const int pl = q / CD, ch = q - pl * CD;
-                    const T* src = (pl < 8 ? gd_in : hd_in) + (long long)(pl & 7) * N + rowoff;
-                    cp_async16(row + (size_t)pl * WW * sizeof(T) + ch * 16, (const unsigned char*)src + ch * 16);
+                    const T* src = (pl < 8 ? gd_in : hd_in) + (long long)(pl & 7) * N + rowoff +
+                                   wrap1(ws + ch * (int)(16 / sizeof(T)), nx);
+                    cp_async16(row + (size_t)pl * WW * sizeof(T) + ch * 16, (const unsigned char*)src);
                 } else if ((q -= 16 * CD) < 2 * CM) {
                     const int pl = q / CM, ch = q - pl * CM;
                     cp_async16(row + ST::D_ROW + (size_t)pl * WW * sizeof(float2) + ch * 16,
-                               (const unsigned char*)((pl == 0 ? gm_in : hm_in) + rowoff) + ch * 16);
+                               (const unsigned char*)((pl == 0 ? gm_in : hm_in) + rowoff + wrap1(ws + 2 * ch, nx)));
                 } else {
                     q -= 2 * CM;
-                    cp_async16(row + ST::D_ROW + ST::M_ROW + q * 16, (const unsigned char*)(php_in + rowoff) + q * 16);
+                    cp_async16(row + ST::D_ROW + ST::M_ROW + q * 16,
+                               (const unsigned char*)(php_in + rowoff + wrap1(ws + 4 * q, nx)));
                 }
             }
             cp_async_commit();
@@ -856,7 +861,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
         ys = y0;
         ye = y1;
         x0 = strip * TX;
-        vec = (x0 - WOFF >= 0) && (x0 - WOFF + WW <= nx) && (nx % VEC == 0);
+        vec = (nx % VEC == 0) && (nx >= WW);   // seam strips wrap chunk by chunk
         __syncthreads();   // the previous piece's last collide read the rings
         issue(0, ys - 3, 4);
         cp_async_wait_all();
