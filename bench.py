@@ -44,6 +44,21 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 BYTES_PER_CELL = {"fp32": 264, "fp16": 132, "bf16": 132}   # algorithmic bytes per cell update
+
+# DRAM bytes (read + write) per step_kernel launch on the 4096 x 2048 shear workload from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the
+# step kernel's sources and float flags: a changed kernel reports null until re-measured.
+TRAFFIC = {"2891d61dbae9317d": {"fp32": 3.14e9, "fp16": 2.10e9, "bf16": 2.10e9}}
+
+
+def kernel_hash():
+    import hashlib
+    from paper_2609_26332_b300 import build as _b
+    h = hashlib.sha256()
+    for f in ("surflbm_step.cuh", "surflbm_device.cuh", "surflbm_api.cu"):
+        h.update(open(os.path.join(_b.CSRC, f), "rb").read())
+    h.update(" ".join(_b.FLOAT_FLAGS).encode())
+    return h.hexdigest()[:16]
 DTYPE = {"fp32": "f32", "fp16": "f16-storage/f32-compute", "bf16": "bf16-storage/f32-compute"}
 
 
@@ -260,8 +275,11 @@ def run_batch(args, rank, world, dist):
             "per_instance_launches": {"value": per_inst, "unit": "MLUPS", "steps": k_inst,
                                       "launches": k_inst * len(specs), "speedup_batched": value / per_inst},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "peak_kind": peak_kind, "bytes_per_cell": BYTES_PER_CELL[args.precision]},
+                         "frac": achieved / peak,
+                         "traffic": (TRAFFIC.get(kernel_hash(), {}).get(args.precision)
+                                     if (args.nx, args.ny) == (4096, 2048) else None),
+                         "peak_kind": peak_kind, "bytes_per_cell": BYTES_PER_CELL[args.precision],
+                         "kernel_hash": kernel_hash()},
             "e2e": {"value": world * cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": 16 * cells / args.steps, "d2h_bytes_per_step": 40 * cells / args.steps},
             "gpu_launches": args.steps,
@@ -453,8 +471,11 @@ def main():
                        "nx": args.nx, "ny": args.ny, "cells": cells, "parallelism": f"replicas{world}",
                        "l2": "state 2.2 GB >> 126 MB L2, no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "peak_kind": peak_kind, "bytes_per_cell": BYTES_PER_CELL[args.precision]},
+                         "frac": achieved / peak,
+                         "traffic": (TRAFFIC.get(kernel_hash(), {}).get(args.precision)
+                                     if (args.nx, args.ny) == (4096, 2048) else None),
+                         "peak_kind": peak_kind, "bytes_per_cell": BYTES_PER_CELL[args.precision],
+                         "kernel_hash": kernel_hash()},
             "e2e": {"value": world * cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": 16 * cells / args.steps, "d2h_bytes_per_step": 40 * cells / args.steps},
             "gpu_launches": args.steps,

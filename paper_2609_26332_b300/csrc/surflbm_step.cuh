@@ -764,9 +764,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
             }
         }
 
-        // ---- the two scalar sets share one code path
-#pragma unroll 1
-        for (int s = 0; s < nsets; ++s) {
+        // ---- the two scalar sets share one code path, unrolled so that the independent
+        // phi and psi collisions interleave (more instruction-level parallelism)
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (s >= nsets) break;
             const float cval = s == 0 ? phi : psi;
             const ff cff = s == 0 ? phff : psff;
             float Rf;
