@@ -1,7 +1,7 @@
 """Benchmark of the coupled phase-field / surfactant / flow LBM step on B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
-                    [--workload shear|batch|warmstart] [--precision fp32|fp16|bf16]
+                    [--workload shear|batch|warmstart|shear-track] [--precision fp32|fp16|bf16]
 
 Workload (default): the sheared sessile drop (top wall at u_w = 0.01, 90 deg contact
 angle, psi0 = 0.02, solid-gas adsorption 0.5, tau = 0.8, eps = 4, FP32) on a
@@ -43,6 +43,8 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+from paper_2609_26332_b300 import ranks  # noqa: E402
+
 BYTES_PER_CELL = {"fp32": 264, "fp16": 132, "bf16": 132}   # algorithmic bytes per cell update
 
 # DRAM bytes (read + write) per step_kernel launch on the 4096 x 2048 shear workload from
@@ -62,6 +64,11 @@ def kernel_hash():
 DTYPE = {"fp32": "f32", "fp16": "f16-storage/f32-compute", "bf16": "bf16-storage/f32-compute"}
 
 
+# the shear configuration's physics: Ca = mu u_w / sigma = 0.5 with tau = 0.8, u_w = 0.01
+# (sigma = 0.002), Pi = 1.35, Ex = 0.5 as in the paper's Couette case (Sec. 4.5)
+SHEAR_SIGMA, SHEAR_EX, SHEAR_PI = 0.002, 0.5, 1.35
+
+
 def shear_case(nx, ny, precision="fp32"):
     R = 480.0 * ny / 2048.0
     return dict(nx=nx, ny=ny, R=R, xc=nx / 4.0, theta=90.0, psi0=0.02, beta_sg=0.5, beta_sl=0.0, u_w=0.01,
@@ -70,13 +77,14 @@ def shear_case(nx, ny, precision="fp32"):
 
 def init_fields(case):
     from paper_2609_26332_b300 import inputs
-    pb = inputs.bulk_phi(case["psi0"], 1.0)
+    pb = inputs.bulk_phi(case["psi0"], SHEAR_EX)
     return inputs.sessile_drop(case["nx"], case["ny"], case["R"], 4.0, xc=case["xc"], phi_b=pb, psi0=case["psi0"])
 
 
 def make_domain(case, stream):
     from paper_2609_26332_b300 import binding as B
-    p = B.default_params(case["nx"], case["ny"], precision=case["precision"], psi_b=case["psi0"])
+    p = B.default_params(case["nx"], case["ny"], precision=case["precision"], psi_b=case["psi0"],
+                         sigma=SHEAR_SIGMA, Ex=SHEAR_EX, Pi=SHEAR_PI)
     d = B.Domain(p, stream=stream)
     d.set_wall(0, case["theta"], case["beta_sg"], case["beta_sl"], 0.0)
     d.set_wall(1, 90.0, 0.0, 0.0, case["u_w"])
@@ -139,7 +147,7 @@ def cpu_baseline(seconds=12.0):
     from oracle import Oracle, OracleParams, Wall
     case = shear_case(512, 256)
     phi0, psi0 = init_fields(case)
-    p = OracleParams(nx=512, ny=256, psi_b=case["psi0"],
+    p = OracleParams(nx=512, ny=256, psi_b=case["psi0"], sigma=SHEAR_SIGMA, Ex=SHEAR_EX, Pi=SHEAR_PI,
                      walls=[Wall(case["theta"], case["beta_sg"], case["beta_sl"], 0.0), Wall(90.0, 0, 0, case["u_w"])])
     o = Oracle(p, phi0, psi0)
     o.step(1)
@@ -159,7 +167,7 @@ def run_reference(args, rank, world):
     from oracle import Oracle, OracleParams, Wall
     case = shear_case(512, 256)
     phi0, psi0 = init_fields(case)
-    p = OracleParams(nx=512, ny=256, psi_b=case["psi0"],
+    p = OracleParams(nx=512, ny=256, psi_b=case["psi0"], sigma=SHEAR_SIGMA, Ex=SHEAR_EX, Pi=SHEAR_PI,
                      walls=[Wall(case["theta"], case["beta_sg"], case["beta_sl"], 0.0), Wall(90.0, 0, 0, case["u_w"])])
     o = Oracle(p, phi0, psi0)
     o.step(args.warmup)
@@ -184,6 +192,7 @@ def run_batch(args, rank, world, dist):
     import ctypes
     import torch
     from paper_2609_26332_b300 import binding as B, inputs
+    # weak scaling: every rank steps its own seeded batch of the same size distribution
     specs = inputs.batch_instances(args.instances, seed=inputs.DEFAULT_SEED + rank)
     params, walls, fields = [], [], []
     for sp in specs:
@@ -217,19 +226,13 @@ def run_batch(args, rank, world, dist):
     torch.cuda.synchronize()
     ms = timed(lambda: b.step(args.steps))
     clocks = sampler.stop() if sampler else None
-    tb = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(tb, op=dist.ReduceOp.MAX)
-    ms_batch = float(tb.item())
+    ms_batch = ranks.max_over_ranks(ms, dist, "cuda")
 
     # the same instances, one launch per instance per step
     k_inst = max(1, args.steps // 4)
     torch.cuda.synchronize()
     ms_inst = timed(lambda: [b.step_instance(i, k_inst) for i in range(len(specs))])
-    ti = torch.tensor([ms_inst], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(ti, op=dist.ReduceOp.MAX)
-    ms_inst = float(ti.item())
+    ms_inst = ranks.max_over_ranks(ms_inst, dist, "cuda")
 
     # end to end: upload every instance from pinned host memory, step, read every field back
     pinned = [(torch.from_numpy(p).pin_memory().numpy(), torch.from_numpy(q).pin_memory().numpy())
@@ -248,10 +251,7 @@ def run_batch(args, rank, world, dist):
                                                  for k in ("phi", "psi", "ux", "uy", "p")])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = ranks.max_over_ranks(e2e_s, dist, "cuda")
     tot_bad = sum(int(b.read_totals(i, check=False)["range_count"]) for i in range(len(specs)))
 
     if rank == 0:
@@ -359,6 +359,34 @@ def run_warmstart(args, rank, world, dist):
     net.close()
 
 
+def run_shear_track(args, rank, world, dist):
+    """The 512 x 256 shear configuration run to its end for three solid-gas adsorption
+    strengths: wetted width on the wall and detachment step, plus the throughput."""
+    import torch
+    from paper_2609_26332_b300 import shear
+    betas = (0.0, 0.5, 1.0)
+    t0 = time.perf_counter()
+    res = shear.track(betas, steps=args.track_steps, every=500)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if rank == 0:
+        cells = 512 * 256 * len(betas)
+        line = {
+            "metric": "sheared-drop contact-line tracking, wall-clock MLUPS", "value": cells * args.track_steps / dt / 1e6,
+            "unit": "MLUPS", "n_gpus": world, "steps": args.track_steps, "warmup": 0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "shear drop 512x256, R=60 at (128, 0), theta0=90, psi0=0.02, top wall 0.01, "
+                                   "beta_sg in {0, 0.5, 1}, beta_sl=0, Ca=0.5 (sigma 0.002), Pi=1.35, Ex=0.5; "
+                                   "three drops in one batch, wall row read every 500 steps"},
+            "tracks": {str(b): {"detach_step": r["detach"], "width_first": r["width"][0], "width_last": r["width"][-1],
+                                "centre_first": r["centre"][0], "centre_last": r["centre"][-1],
+                                "width_every_5000": r["width"][9::10], "kinetic_final": r["kinetic"],
+                                "range_count": r["range_count"]} for b, r in res.items()},
+            "gpu_launches": args.track_steps,
+        }
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -369,7 +397,8 @@ def main():
     ap.add_argument("--ny", type=int, default=2048)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="shear", choices=["shear", "batch", "warmstart"])
+    ap.add_argument("--workload", default="shear", choices=["shear", "batch", "warmstart", "shear-track"])
+    ap.add_argument("--track-steps", type=int, default=50000)
     ap.add_argument("--ws-train", type=int, default=4096)
     ap.add_argument("--ws-eval", type=int, default=256)
     ap.add_argument("--ws-epochs", type=int, default=60)
@@ -383,9 +412,7 @@ def main():
     ap.add_argument("--tiling-cache", default=None)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = ranks.rank_world()
 
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -400,8 +427,9 @@ def main():
     from paper_2609_26332_b300 import build as _build
     _build.build()
     from paper_2609_26332_b300 import binding as B
-    if args.workload in ("batch", "warmstart"):
-        (run_batch if args.workload == "batch" else run_warmstart)(args, rank, world, dist)
+    if args.workload in ("batch", "warmstart", "shear-track"):
+        {"batch": run_batch, "warmstart": run_warmstart, "shear-track": run_shear_track}[args.workload](
+            args, rank, world, dist)
         if dist:
             dist.destroy_process_group()
         return
@@ -429,10 +457,7 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1)
     clocks = sampler.stop() if sampler else None
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = ranks.max_over_ranks(ms, dist, "cuda")
     tot = d.read_totals(check=False)
 
     # end to end through the C ABI with host buffers: upload, step, read back
@@ -451,10 +476,7 @@ def main():
                                    for k in ("phi", "psi", "ux", "uy", "p")])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = ranks.max_over_ranks(e2e_s, dist, "cuda")
 
     if rank == 0:
         peak, peak_kind = measured_peaks()

@@ -1,0 +1,118 @@
+"""The precision configuration at scale, and many small drops.
+
+* Sheared drop 2048 x 1024 (R = 240), 10,000 steps: FP16 / BF16 deviation storage
+  against the FP32 path, per field, with the conserved totals; and the 512 x 256 analog
+  against the FP64 oracle for all three storage modes (the oracle is too slow at full
+  size).
+* Sixteen drops of radius 8-16 (seeded, non-overlapping) in a 256 x 256 box with neutral
+  walls: the per-drop change of the geometric area (zero-level set, Sec. 4.1 triangle
+  split) is smaller with the nonlinear constraint than with the linear one, whose
+  curvature-dependent bulk shift shrinks small drops (Sec. 2.3, Sec. 4.2).
+"""
+import numpy as np
+import pytest
+from scipy import ndimage
+
+pytestmark = pytest.mark.gpu
+
+import bench
+from oracle import Oracle, OracleParams, Wall
+from oracle.analysis import zero_level_area
+
+
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _shear_domain(nx, ny, precision):
+    case = bench.shear_case(nx, ny, precision)
+    d = bench.make_domain(case, None)
+    d.init_fields(*bench.init_fields(case))
+    return d
+
+
+def test_precision_modes_at_2048x1024_against_fp32():
+    _cuda()
+    fields, totals = {}, {}
+    for prec in ("fp32", "fp16", "bf16"):
+        with _shear_domain(2048, 1024, prec) as d:
+            d.step(10000)
+            fields[prec] = d.read_fields()
+            totals[prec] = d.read_totals()
+    ref = fields["fp32"]
+    umax = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
+    for prec in ("fp16", "bf16"):
+        f = fields[prec]
+        e = {k: float(np.abs(f[k] - ref[k]).max()) for k in ("phi", "psi")}
+        e["u_rel"] = float(max(np.abs(f["ux"] - ref["ux"]).max(), np.abs(f["uy"] - ref["uy"]).max()) / umax)
+        e["phi_rms"] = float(np.sqrt(np.mean((f["phi"] - ref["phi"]) ** 2)))
+        dpsi = abs(totals[prec]["psi_total"] - totals["fp32"]["psi_total"]) / totals["fp32"]["psi_total"]
+        print(f"2048x1024 shear, 10000 steps, {prec} vs fp32: {e}, sum psi rel {dpsi:.2e}")
+        assert dpsi < 1e-10
+        assert totals[prec]["range_count"] == 0
+        assert e["phi_rms"] < (2e-3 if prec == "fp16" else 2e-2)
+
+
+@pytest.fixture(scope="module")
+def oracle_512():
+    case = bench.shear_case(512, 256)
+    phi0, psi0 = bench.init_fields(case)
+    p = OracleParams(nx=512, ny=256, psi_b=case["psi0"], sigma=bench.SHEAR_SIGMA, Ex=bench.SHEAR_EX,
+                     Pi=bench.SHEAR_PI,
+                     walls=[Wall(case["theta"], case["beta_sg"], case["beta_sl"], 0.0), Wall(90.0, 0, 0, case["u_w"])])
+    o = Oracle(p, phi0, psi0)
+    o.step(400)
+    return o.fields(), o.totals()
+
+
+@pytest.mark.parametrize("prec,bound", [("fp32", 1e-5), ("fp16", 2e-3), ("bf16", 2e-2)])
+def test_shear_512x256_analog_against_the_oracle(prec, bound, oracle_512):
+    _cuda()
+    fo, to = oracle_512
+    with _shear_domain(512, 256, prec) as d:
+        d.step(400)
+        fg = d.read_fields()
+        tg = d.read_totals()
+    e = {k: float(np.abs(fg[k] - fo[k]).max()) for k in ("phi", "psi")}
+    umax = max(np.abs(fo["ux"]).max(), np.abs(fo["uy"]).max())
+    e["u_rel"] = float(max(np.abs(fg["ux"] - fo["ux"]).max(), np.abs(fg["uy"] - fo["uy"]).max()) / umax)
+    print(f"512x256 shear, 400 steps, {prec} vs oracle: {e}")
+    assert e["phi"] < bound and e["psi"] < bound
+    assert abs(tg["psi_total"] - to["psi_total"]) <= 1e-10 * to["psi_total"]
+
+
+def _drop_areas(phi):
+    lab, n = ndimage.label(phi > 0)
+    return sorted(float(zero_level_area(np.where(lab == k, phi, -np.abs(phi)))) for k in range(1, n + 1))
+
+
+def test_many_small_drops_keep_their_area_better_with_the_nonlinear_constraint():
+    """Both constraints held exactly in total (target mode), so what differs is how each
+    drop's area moves: the linear constraint's bulk shift (proportional to eps / R)
+    takes area from the small drops.  Over long times every small drop of this size
+    (R / eps = 2-4) exchanges area with the others through the global multiplier in
+    either model, so the comparison is made early, after 300 steps."""
+    _cuda()
+    from paper_2609_26332_b300 import binding as B, inputs
+    phi0, drops = inputs.drop_field(256, 256, 16, 8.0, 16.0, 4.0, 8.0, seed=31)
+    assert len(drops) == 16
+    err = {}
+    for constraint in (B.NONLINEAR, B.LINEAR):
+        p = B.default_params(256, 256, psi_on=0, constraint=constraint, multiplier=B.TARGET)
+        with B.Domain(p) as d:
+            d.init_fields(phi0)
+            a0 = np.array(_drop_areas(d.read_fields()["phi"]))
+            assert len(a0) == 16
+            series = []
+            for n in (100, 200, 300, 1000):
+                d.step(n - (series[-1][0] if series else 0))
+                a = _drop_areas(d.read_fields()["phi"])
+                a = np.array(sorted(a + [0.0] * (16 - len(a))))[:16]
+                series.append((n, float(np.mean(np.abs(a - a0) / a0))))
+        err[constraint] = dict(series)
+    print(f"16 drops R 8-16, mean per-drop area change by step: nonlinear {err[B.NONLINEAR]}, "
+          f"linear {err[B.LINEAR]}")
+    assert err[B.NONLINEAR][300] < err[B.LINEAR][300]
