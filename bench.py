@@ -1,7 +1,7 @@
 """Benchmark of the coupled phase-field / surfactant / flow LBM step on B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
-                    [--workload shear|batch|warmstart|shear-track] [--precision fp32|fp16|bf16]
+                    [--workload shear|batch|warmstart|shear-track|conv] [--precision fp32|fp16|bf16]
 
 Workload (default): the sheared sessile drop (top wall at u_w = 0.01, 90 deg contact
 angle, psi0 = 0.02, solid-gas adsorption 0.5, tau = 0.8, eps = 4, FP32) on a
@@ -22,6 +22,13 @@ strengths U[0,1], radius U[0.25,0.35] ny) are relaxed from cold starts by the ba
 solver, the encoder-decoder is trained on the relaxed fields with the tensor-core
 kernels, and held-out drops are relaxed from cold and from warm starts; the value is
 the median ratio of cold to warm steps to equilibrium.
+
+Workload 'shear-track': the 512 x 256 shear configuration run to 50,000 steps for three
+solid-gas adsorption strengths (one batch), tracking the wetted segment on the wall.
+
+Workload 'conv': throughput of the warm-start network's tensor-core convolutions
+(forward, input gradient, weight gradient) on its heaviest layers, against the BF16
+tensor peak.
 
 Prints one JSON line (rank 0).  Metric: MLUPS (million lattice-node updates per
 second, whole job).  Under torchrun with N > 1 every rank steps its own replica of the
@@ -61,6 +68,8 @@ def kernel_hash():
         h.update(open(os.path.join(_b.CSRC, f), "rb").read())
     h.update(" ".join(_b.FLOAT_FLAGS).encode())
     return h.hexdigest()[:16]
+
+
 DTYPE = {"fp32": "f32", "fp16": "f16-storage/f32-compute", "bf16": "bf16-storage/f32-compute"}
 
 
@@ -140,6 +149,16 @@ def measured_peaks():
         j = json.load(open(path))
         return float(j["hbm_gbs"]), "measured"
     return 6400.0, "fallback"
+
+
+def measured_bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s): the burst figure (kernels timed alone)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        j = json.load(open(path))
+        if "bf16_tflops" in j:
+            return float(j["bf16_tflops"]), "measured"
+    return 1800.0, "fallback"
 
 
 def cpu_baseline(seconds=12.0):
@@ -387,6 +406,66 @@ def run_shear_track(args, rank, world, dist):
         print(json.dumps(line))
 
 
+# the heaviest 3 x 3 convs of the warm-start network on 256 x 128 fields, batch 32:
+# (level, Cin, Cout) of the decoder's first convs and one conv of each level
+CONV_LAYERS = [(0, 96, 32), (1, 192, 64), (2, 256, 128), (0, 32, 32), (1, 64, 64), (2, 128, 128)]
+
+
+def run_conv(args, rank, world, dist):
+    """Tensor-core convolution throughput: forward, input gradient and weight gradient
+    of the warm-start network's heaviest layers (BF16 operands, FP32 accumulation)."""
+    import torch
+    from paper_2609_26332_b300 import binding as B
+    torch.manual_seed(rank)
+    Bn, H0, W0 = 32, 128, 256
+    rows, tot_flop, tot_ms = [], 0.0, 0.0
+    st = torch.cuda.current_stream()
+    launches = 0
+    for lv, ci, co in CONV_LAYERS:
+        H, W = H0 >> lv, W0 >> lv
+        x = torch.randn(Bn, H, W, ci, device="cuda").to(torch.bfloat16)
+        w = (torch.randn(co, 3, 3, ci, device="cuda") * (2.0 / (9 * ci)) ** 0.5).to(torch.bfloat16)
+        wt = torch.empty(ci, 3, 3, co, device="cuda", dtype=torch.bfloat16)
+        y = torch.empty(Bn, H, W, co, device="cuda", dtype=torch.bfloat16)
+        dx = torch.empty_like(x)
+        dw = torch.zeros(co, 3, 3, ci, device="cuda", dtype=torch.float32)
+        B.conv3x3_flip_weights(w, wt)
+        flop = 2.0 * Bn * H * W * 9 * ci * co
+        ops = {"forward": lambda: B.conv3x3_forward(x, w, None, y, relu=True),
+               "input_grad": lambda: B.conv3x3_input_grad(y, wt, x, dx),
+               "weight_grad": lambda: B.conv3x3_weight_grad(x, y, dw)}
+        for name, fn in ops.items():
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(args.steps):
+                fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = ranks.max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+            launches += args.steps
+            rows.append({"layer": f"{H}x{W} {ci}->{co}", "op": name, "us": ms * 1e3, "tflops": flop / ms / 1e9})
+            tot_flop += flop
+            tot_ms += ms
+        assert B.conv_error() == 0
+    if rank == 0:
+        peak, kind = measured_bf16_peak()
+        achieved = tot_flop / tot_ms / 1e9
+        print(json.dumps({
+            "metric": "warm-start conv throughput (fwd + input grad + weight grad)", "value": world * achieved,
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16-operands/f32-accumulate", "data": "synthetic",
+            "config": {"workload": "3x3 convs of the warm-start network, batch 32 of 256x128 fields: "
+                                   + ", ".join(f"level {lv} {ci}->{co}" for lv, ci, co in CONV_LAYERS)},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": kind},
+            "layers": rows, "gpu_launches": launches,
+        }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,7 +476,7 @@ def main():
     ap.add_argument("--ny", type=int, default=2048)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="shear", choices=["shear", "batch", "warmstart", "shear-track"])
+    ap.add_argument("--workload", default="shear", choices=["shear", "batch", "warmstart", "shear-track", "conv"])
     ap.add_argument("--track-steps", type=int, default=50000)
     ap.add_argument("--ws-train", type=int, default=4096)
     ap.add_argument("--ws-eval", type=int, default=256)
@@ -427,8 +506,8 @@ def main():
     from paper_2609_26332_b300 import build as _build
     _build.build()
     from paper_2609_26332_b300 import binding as B
-    if args.workload in ("batch", "warmstart", "shear-track"):
-        {"batch": run_batch, "warmstart": run_warmstart, "shear-track": run_shear_track}[args.workload](
+    if args.workload in ("batch", "warmstart", "shear-track", "conv"):
+        {"batch": run_batch, "warmstart": run_warmstart, "shear-track": run_shear_track, "conv": run_conv}[args.workload](
             args, rank, world, dist)
         if dist:
             dist.destroy_process_group()
