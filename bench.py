@@ -480,12 +480,12 @@ def main():
     ap.add_argument("--track-steps", type=int, default=50000)
     ap.add_argument("--ws-train", type=int, default=4096)
     ap.add_argument("--ws-eval", type=int, default=256)
-    ap.add_argument("--ws-epochs", type=int, default=60)
+    ap.add_argument("--ws-epochs", type=int, default=300)
     ap.add_argument("--ws-batch", type=int, default=32)
     ap.add_argument("--ws-lr", type=float, default=2e-3)
-    ap.add_argument("--ws-tol", type=float, default=1e-7)
+    ap.add_argument("--ws-tol", type=float, default=1e-6)
     ap.add_argument("--ws-eval-tol", type=float, default=1e-6)
-    ap.add_argument("--ws-max-steps", type=int, default=40000)
+    ap.add_argument("--ws-max-steps", type=int, default=30000)
     ap.add_argument("--instances", type=int, default=512)
     ap.add_argument("--graph-steps", type=int, default=32)
     ap.add_argument("--tiling-cache", default=None)

@@ -131,27 +131,40 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv_mk_kernel(const MKArgs a
         py = (int)(t % a.H);
         pimg = t / a.H;
     }
+    // gather set-up, once per thread: the own pixel's element offset, which of the 9 taps
+    // land inside the image, and the weight rows this thread copies
+    const __nv_bfloat16* own = a.x + (mvalid ? m * C : 0);
+    unsigned vmask = 0;
+    if (mvalid) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
+            if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) vmask |= 1u << t;
+        }
+    }
+    const long long rowC = (long long)a.W * C;
+    const bool brow0 = tid < N, brow1 = tid + CONV_THREADS < N;
+    const __nv_bfloat16* wrow0 = brow0 ? a.w + (size_t)tid * KC * 8 : a.w;
+    const __nv_bfloat16* wrow1 = brow1 ? a.w + (size_t)(tid + CONV_THREADS) * KC * 8 : a.w;
+    auto tap_offset = [&](int tap) { return (long long)(tap / 3 - 1) * rowC + (long long)(tap % 3 - 1) * C; };
     auto load = [&](int kb) {
         const uint32_t sA = sbase + (uint32_t)(kb % CONV_STAGES) * stage, sB = sA + A_STAGE_BYTES;
-        int kc = kb * 8;
+        const int kc = kb * 8;
         int tap = kc / CB, cb = kc - tap * CB;
-#pragma unroll 1
-        for (int c = 0; c < 8; ++c, ++kc) {
-            const bool kv = kc < KC;
-            bool v = mvalid && kv;
-            const __nv_bfloat16* src = a.x;
-            if (v) {
-                const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
-                v = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-                if (v) src = a.x + (((pimg * a.H + yy) * a.W + xx) * C + cb * 8);
-            }
-            cp16_ca(sA + (uint32_t)c * 2048u + (uint32_t)tid * 16u, src, v);
-            for (int n = tid; n < N; n += CONV_THREADS)
-                cp16_cg(sB + (uint32_t)c * (uint32_t)(16 * N) + (uint32_t)n * 16u,
-                        kv ? a.w + ((size_t)n * KC + kc) * 8 : a.w, kv);
+        long long toff = tap_offset(tap);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int k = kc + c;
+            const bool kv = k < KC;
+            const bool v = kv && ((vmask >> tap) & 1u);
+            cp16_ca(sA + (uint32_t)c * 2048u + (uint32_t)tid * 16u, v ? own + toff + cb * 8 : a.x, v);
+            const uint32_t bdst = sB + (uint32_t)c * (uint32_t)(16 * N) + (uint32_t)tid * 16u;
+            if (brow0) cp16_cg(bdst, kv ? wrow0 + (size_t)k * 8 : a.w, kv);
+            if (brow1) cp16_cg(bdst + (uint32_t)CONV_THREADS * 16u, kv ? wrow1 + (size_t)k * 8 : a.w, kv);
             if (++cb == CB) {
                 cb = 0;
                 ++tap;
+                toff = tap_offset(tap);
             }
         }
     };
@@ -248,27 +261,33 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv_wg_kernel(const WGArgs a
     const uint32_t tmem = S.tmem;
 
     const int pl = tid & 63, gsub = tid >> 6;
-    auto load = [&](int kb) {
+    // this thread's pixel of K block 0; every block advances it by 64 pixels
+    int cx = 0, cy = 0;
+    {
+        const long long p = p0 + pl;
+        cx = (int)(p % a.W);
+        cy = (int)((p / a.W) % a.H);
+    }
+    long long pcur = p0 + pl;
+    const uint32_t qoffA = (uint32_t)(pl >> 3) * 2048u + (uint32_t)(pl & 7) * 16u;
+    const uint32_t qoffB = (uint32_t)(pl >> 3) * (uint32_t)(16 * C) + (uint32_t)(pl & 7) * 16u;
+    const long long dxy = (long long)dy * a.W + dx;
+    auto load = [&](int kb) {   // called with kb = 0, 1, 2, ... in order
         const uint32_t sA = sbase + (uint32_t)(kb % CONV_STAGES) * stage, sB = sA + A_STAGE_BYTES;
-        const long long p = p0 + (long long)kb * 64 + pl;
-        const bool pv = p < p1;
-        bool xv = false;
-        long long xoff = 0;
-        if (pv) {
-            const int px = (int)(p % a.W);
-            const long long t = p / a.W;
-            const int py = (int)(t % a.H);
-            const long long img = t / a.H;
-            const int yy = py + dy, xx = px + dx;
-            xv = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-            if (xv) xoff = ((img * a.H + yy) * a.W + xx) * C;
-        }
-        const uint32_t qoffA = (uint32_t)(pl >> 3) * 2048u + (uint32_t)(pl & 7) * 16u;
-        const uint32_t qoffB = (uint32_t)(pl >> 3) * (uint32_t)(16 * C) + (uint32_t)(pl & 7) * 16u;
+        const bool pv = pcur < p1;
+        const int yy = cy + dy, xx = cx + dx;
+        const bool xv = pv && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+        const long long xoff = xv ? (pcur + dxy) * C : 0;
         for (int g = gsub; g < Co / 8; g += 2)
-            cp16_cg(sA + qoffA + (uint32_t)g * 128u, pv ? a.dz + (size_t)p * Co + g * 8 : a.dz, pv);
+            cp16_cg(sA + qoffA + (uint32_t)g * 128u, pv ? a.dz + (size_t)pcur * Co + g * 8 : a.dz, pv);
         for (int h = gsub; h < C / 8; h += 2)
             cp16_ca(sB + qoffB + (uint32_t)h * 128u, xv ? a.x + xoff + h * 8 : a.x, xv);
+        pcur += 64;
+        cx += 64;
+        while (cx >= a.W) {
+            cx -= a.W;
+            if (++cy == a.H) cy = 0;
+        }
     };
 
     const uint32_t idesc = idesc_bf16(128, C, true, true);
