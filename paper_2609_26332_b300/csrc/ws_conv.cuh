@@ -17,7 +17,7 @@
 namespace ws {
 
 constexpr int CONV_THREADS = 128;
-constexpr int CONV_STAGES = 4;
+constexpr int CONV_STAGES = 4;      // deepest ring; 32-channel tiles use 3 (three CTAs per SM)
 constexpr uint32_t A_STAGE_BYTES = 128 * 64 * 2;     // 128 rows x 64 K-elements
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;      // 2 s: far beyond any legitimate wait
 
@@ -71,13 +71,14 @@ __device__ __forceinline__ void pipe_open(Pipe& S, uint32_t ncols) {
 }
 
 // drain after the main loop: wait (bounded) for the last committed MMA group
+template <int STAGES>
 __device__ __forceinline__ bool pipe_drain(Pipe& S, unsigned int* err) {
     cp_wait<0>();
     __syncthreads();
     const int last = S.last;
     bool ok = !S.abort;
     if (last >= 0) {
-        const bool done = mbar_wait(&S.bar[last % CONV_STAGES], (uint32_t)(last / CONV_STAGES) & 1u, WAIT_LIMIT_NS);
+        const bool done = mbar_wait(&S.bar[last % STAGES], (uint32_t)(last / STAGES) & 1u, WAIT_LIMIT_NS);
         if (!done) {
             ok = false;
             atomicOr(err, ERR_TIMEOUT);
@@ -110,6 +111,7 @@ __device__ __forceinline__ void issue_block(uint32_t tmem, uint32_t sA, uint32_t
 // ------------------------------------------------------------------ forward / input gradient
 // A (pixels x K, K-major): core matrix (row group g, K chunk c) at c * 2048 + g * 128.
 // B (N x K, K-major):      core matrix (row group h, K chunk c) at c * 16 N + h * 128.
+template <int STAGES>
 __global__ void __launch_bounds__(CONV_THREADS, 1) conv_mk_kernel(const MKArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ Pipe S;
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv_mk_kernel(const MKArgs a
     const __nv_bfloat16* wrow1 = brow1 ? a.w + (size_t)(tid + CONV_THREADS) * KC * 8 : a.w;
     auto tap_offset = [&](int tap) { return (long long)(tap / 3 - 1) * rowC + (long long)(tap % 3 - 1) * C; };
     auto load = [&](int kb) {
-        const uint32_t sA = sbase + (uint32_t)(kb % CONV_STAGES) * stage, sB = sA + A_STAGE_BYTES;
+        const uint32_t sA = sbase + (uint32_t)(kb % STAGES) * stage, sB = sA + A_STAGE_BYTES;
         const int kc = kb * 8;
         int tap = kc / CB, cb = kc - tap * CB;
         long long toff = tap_offset(tap);
@@ -170,26 +172,26 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv_mk_kernel(const MKArgs a
     };
 
     const uint32_t idesc = idesc_bf16(128, N, false, false);
-    for (int kb = 0; kb < CONV_STAGES - 1; ++kb) {
+    for (int kb = 0; kb < STAGES - 1; ++kb) {
         if (kb < NKB) load(kb);
         cp_commit();
     }
     for (int kb = 0; kb < NKB; ++kb) {
-        cp_wait<CONV_STAGES - 2>();
+        cp_wait<STAGES - 2>();
         fence_async_smem();
         __syncthreads();
         if (S.abort) break;
         if (tid == 0) {
             tc_fence_after();
-            const uint32_t sA = sbase + (uint32_t)(kb % CONV_STAGES) * stage;
+            const uint32_t sA = sbase + (uint32_t)(kb % STAGES) * stage;
             issue_block(tmem, sA, sA + A_STAGE_BYTES, 2048u, 128u, (uint32_t)(16 * N), 128u, idesc, kb == 0);
-            mma_commit(&S.bar[kb % CONV_STAGES]);
+            mma_commit(&S.bar[kb % STAGES]);
             S.last = kb;
         }
-        const int kn = kb + CONV_STAGES - 1;
+        const int kn = kb + STAGES - 1;
         if (kn < NKB) {
             bool ok = true;
-            if (kb >= 1) ok = mbar_wait(&S.bar[(kb - 1) % CONV_STAGES], (uint32_t)((kb - 1) / CONV_STAGES) & 1u, WAIT_LIMIT_NS);
+            if (kb >= 1) ok = mbar_wait(&S.bar[(kb - 1) % STAGES], (uint32_t)((kb - 1) / STAGES) & 1u, WAIT_LIMIT_NS);
             if (ok) load(kn);
             else {
                 S.abort = 1;
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv_mk_kernel(const MKArgs a
         }
         cp_commit();
     }
-    const bool ok = pipe_drain(S, a.err);
+    const bool ok = pipe_drain<STAGES>(S, a.err);
     if (ok) {
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         for (int j = 0; j < N / 16; ++j) {
@@ -238,6 +240,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv_mk_kernel(const MKArgs a
 // A (Cout x pixels, MN-major): core matrix (channel group g, pixel group q) at q * 2048 + g * 128.
 // B (Cin x pixels, MN-major):  core matrix (channel group h, pixel group q) at q * 16 C + h * 128.
 // grid: (pixel splits, 9 taps)
+template <int STAGES>
 __global__ void __launch_bounds__(CONV_THREADS, 1) conv_wg_kernel(const WGArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ Pipe S;
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv_wg_kernel(const WGArgs a
     const uint32_t stage = wg_stage_bytes(C), ncols = tmem_cols_for(C);
     const uint32_t sbase = smem_u32(smem);
     // rows Co..127 of A stay zero in every stage
-    for (int s = 0; s < CONV_STAGES; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
         unsigned char* sa = smem + (size_t)s * stage;
         for (int q = 0; q < 8; ++q)
             for (int g = Co / 8 + (tid >> 3); g < 16; g += CONV_THREADS / 8)
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv_wg_kernel(const WGArgs a
     const uint32_t qoffB = (uint32_t)(pl >> 3) * (uint32_t)(16 * C) + (uint32_t)(pl & 7) * 16u;
     const long long dxy = (long long)dy * a.W + dx;
     auto load = [&](int kb) {   // called with kb = 0, 1, 2, ... in order
-        const uint32_t sA = sbase + (uint32_t)(kb % CONV_STAGES) * stage, sB = sA + A_STAGE_BYTES;
+        const uint32_t sA = sbase + (uint32_t)(kb % STAGES) * stage, sB = sA + A_STAGE_BYTES;
         const bool pv = pcur < p1;
         const int yy = cy + dy, xx = cx + dx;
         const bool xv = pv && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
@@ -291,26 +294,26 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv_wg_kernel(const WGArgs a
     };
 
     const uint32_t idesc = idesc_bf16(128, C, true, true);
-    for (int kb = 0; kb < CONV_STAGES - 1; ++kb) {
+    for (int kb = 0; kb < STAGES - 1; ++kb) {
         if (kb < NKB) load(kb);
         cp_commit();
     }
     for (int kb = 0; kb < NKB; ++kb) {
-        cp_wait<CONV_STAGES - 2>();
+        cp_wait<STAGES - 2>();
         fence_async_smem();
         __syncthreads();
         if (S.abort) break;
         if (tid == 0) {
             tc_fence_after();
-            const uint32_t sA = sbase + (uint32_t)(kb % CONV_STAGES) * stage;
+            const uint32_t sA = sbase + (uint32_t)(kb % STAGES) * stage;
             issue_block(tmem, sA, sA + A_STAGE_BYTES, 2048u, 128u, (uint32_t)(16 * C), 128u, idesc, kb == 0);
-            mma_commit(&S.bar[kb % CONV_STAGES]);
+            mma_commit(&S.bar[kb % STAGES]);
             S.last = kb;
         }
-        const int kn = kb + CONV_STAGES - 1;
+        const int kn = kb + STAGES - 1;
         if (kn < NKB) {
             bool ok = true;
-            if (kb >= 1) ok = mbar_wait(&S.bar[(kb - 1) % CONV_STAGES], (uint32_t)((kb - 1) / CONV_STAGES) & 1u, WAIT_LIMIT_NS);
+            if (kb >= 1) ok = mbar_wait(&S.bar[(kb - 1) % STAGES], (uint32_t)((kb - 1) / STAGES) & 1u, WAIT_LIMIT_NS);
             if (ok) load(kn);
             else {
                 S.abort = 1;
@@ -319,7 +322,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv_wg_kernel(const WGArgs a
         }
         cp_commit();
     }
-    const bool ok = pipe_drain(S, a.err);
+    const bool ok = pipe_drain<STAGES>(S, a.err);
     if (ok && NKB > 0) {
         const int co = warp * 32 + (tid & 31);
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);

@@ -422,14 +422,19 @@ __global__ void project_kernel(const ProjArgs* __restrict__ args) {
 }
 
 // ================================================================== conv launchers
+// ring depth by width: the narrowest tiles (32 channels) take 3 stages, so three CTAs
+// fit on an SM (measured: faster at 32 channels, slower at 64)
+inline int mk_stages(int N) { return N <= 32 ? 3 : 4; }
+inline int wg_stages(int C) { return C <= 32 ? 3 : 4; }
+
 cudaError_t conv_attrs() {
     static cudaError_t done = cudaErrorNotReady;
     if (done == cudaErrorNotReady) {
-        done = cudaFuncSetAttribute(conv_mk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(CONV_STAGES * mk_stage_bytes(256)));
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(conv_wg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(CONV_STAGES * wg_stage_bytes(256)));
+        const int mk = (int)(CONV_STAGES * mk_stage_bytes(256)), wg = (int)(CONV_STAGES * wg_stage_bytes(256));
+        done = cudaFuncSetAttribute(conv_mk_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mk);
+        if (done == cudaSuccess) done = cudaFuncSetAttribute(conv_mk_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mk);
+        if (done == cudaSuccess) done = cudaFuncSetAttribute(conv_wg_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, wg);
+        if (done == cudaSuccess) done = cudaFuncSetAttribute(conv_wg_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, wg);
     }
     return done;
 }
@@ -440,7 +445,9 @@ cudaError_t launch_mk(const bf16* x, const bf16* w, const float* bias, const bf1
     if (e != cudaSuccess) return e;
     MKArgs a{x, w, bias, mask, y, B, H, W, C, N, relu, err};
     const long long P = (long long)B * H * W;
-    conv_mk_kernel<<<(unsigned)((P + 127) / 128), CONV_THREADS, CONV_STAGES * mk_stage_bytes(N), st>>>(a);
+    const unsigned grid = (unsigned)((P + 127) / 128);
+    if (mk_stages(N) == 3) conv_mk_kernel<3><<<grid, CONV_THREADS, 3 * mk_stage_bytes(N), st>>>(a);
+    else conv_mk_kernel<4><<<grid, CONV_THREADS, 4 * mk_stage_bytes(N), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -455,7 +462,8 @@ cudaError_t launch_wg(const bf16* x, const bf16* dz, float* dw, int B, int H, in
     if (ppc < 256) ppc = 256;
     WGArgs a{x, dz, dw, B, H, W, C, N, ppc, err};
     dim3 grid((unsigned)((P + ppc - 1) / ppc), 9);
-    conv_wg_kernel<<<grid, CONV_THREADS, CONV_STAGES * wg_stage_bytes(C), st>>>(a);
+    if (wg_stages(C) == 3) conv_wg_kernel<3><<<grid, CONV_THREADS, 3 * wg_stage_bytes(C), st>>>(a);
+    else conv_wg_kernel<4><<<grid, CONV_THREADS, 4 * wg_stage_bytes(C), st>>>(a);
     return cudaGetLastError();
 }
 
