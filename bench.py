@@ -480,7 +480,7 @@ def main():
     ap.add_argument("--track-steps", type=int, default=50000)
     ap.add_argument("--ws-train", type=int, default=4096)
     ap.add_argument("--ws-eval", type=int, default=256)
-    ap.add_argument("--ws-epochs", type=int, default=300)
+    ap.add_argument("--ws-epochs", type=int, default=600)
     ap.add_argument("--ws-batch", type=int, default=32)
     ap.add_argument("--ws-lr", type=float, default=2e-3)
     ap.add_argument("--ws-tol", type=float, default=1e-6)
