@@ -12,8 +12,10 @@
  * and judges the prediction.
  *
  * Network (fixed architecture, ny and nx divisible by 8):
- *   input  8 channels: the 5 normalised parameters, x and y coordinates, a constant 1
- *   level 0 (ny x nx):          conv 8->32, conv 32->32        (skip e0)
+ *   input 16 channels: the 5 normalised parameters and 11 fixed coordinate features
+ *          (x, y, 1, x^2, y^2, xy, |x|, sin/cos(pi x / 2), sin/cos(pi y / 2); x, y scaled
+ *          by ny / 2, x centred)
+ *   level 0 (ny x nx):          conv 16->32, conv 32->32       (skip e0)
  *   level 1 (ny/2 x nx/2):      avgpool, conv 32->64, 64->64   (skip e1)
  *   level 2 (ny/4 x nx/4):      avgpool, conv 64->128, 128->128 (skip e2)
  *   level 3 (ny/8 x nx/8):      avgpool, conv 128->128, 128->128
