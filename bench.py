@@ -37,6 +37,7 @@ workload ('replicas only': the single-domain path has no multi-GPU exchange here
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -56,8 +57,8 @@ BYTES_PER_CELL = {"fp32": 264, "fp16": 132, "bf16": 132}   # algorithmic bytes p
 
 # DRAM bytes (read + write) per step_kernel launch on the 4096 x 2048 shear workload from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the
-# step kernel's sources and float flags: a changed kernel reports null until re-measured.
-TRAFFIC = {"2891d61dbae9317d": {"fp32": 3.14e9, "fp16": 2.10e9, "bf16": 2.10e9}}
+# step kernel's code (comments stripped) and float flags: a changed kernel reports null until re-measured.
+TRAFFIC = {"929333c44eee5d20": {"fp32": 3.14e9, "fp16": 2.10e9, "bf16": 2.10e9}}
 
 
 def kernel_hash():
@@ -65,7 +66,11 @@ def kernel_hash():
     from paper_2609_26332_b300 import build as _b
     h = hashlib.sha256()
     for f in ("surflbm_step.cuh", "surflbm_device.cuh", "surflbm_api.cu"):
-        h.update(open(os.path.join(_b.CSRC, f), "rb").read())
+        src = open(os.path.join(_b.CSRC, f)).read()
+        # code only: comments and layout do not change the kernel the counters were taken on
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     h.update(" ".join(_b.FLOAT_FLAGS).encode())
     return h.hexdigest()[:16]
 

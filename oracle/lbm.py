@@ -14,7 +14,7 @@ history needed by the source terms.  Each step:
 
 1.  moments phi = sum g, psi = sum h (Sec. 3, macroscopic quantities);
 2.  wall ghost rows for phi, psi from the natural boundary conditions (Eq. boundary,
-    reading c2 in DESIGN.md);
+    closed by ghost rows as below);
 3.  chemical potentials mu_phi, mu_psi (Eqs. eq_muphi, eq_mupsi) with the isotropic
     Laplacian (Sec. 3, stencils);
 4.  the Lagrange multipliers lambda_phi = int h' mu / int h'^2 (Eq. eq15) and
@@ -23,9 +23,9 @@ history needed by the source terms.  Each step:
     pressure (Sec. 3, macroscopic quantities);
 6.  equilibria, source terms and the MRT collision of all three sets (Sec. 3);
 7.  streaming: halfway bounce-back with the moving-wall term for the flow set,
-    specular reflection for the two scalar sets (reading c2).
+    specular reflection for the two scalar sets.
 
-Wall closure (the paper cites an external scheme and does not print it; reading c2):
+Wall closure (the paper cites an external scheme and does not print it):
 ghost rows phi_G = phi_0 - (df_w/dphi)/kappa and psi_G = psi_0 - (df_w/dpsi)/lambda_s
 evaluated with the wall-row values; mu and rho use mirror ghosts.  Because
 bounce-back gives the lattice diffusion a zero wall flux, the wall flux of the
@@ -155,7 +155,7 @@ class Oracle:
         return np.where(on_sg, t_sg, -0.5), np.where(on_sl, t_sl, -0.5), on_sg, on_sl
 
     def _wall_ghosts(self, phi, psi):
-        """Ghost rows (bottom at j = -1, top at j = ny) from Eq. boundary (reading c2)."""
+        """Ghost rows (bottom at j = -1, top at j = ny) from Eq. boundary."""
         d, p = self.d, self.p
         out = []
         for w, row in ((0, 0), (1, self.ny - 1)):
@@ -212,7 +212,7 @@ class Oracle:
         return new
 
     def _stream_scalar(self, post):
-        """Pull streaming of a scalar set with specular walls (reading c2): a link whose
+        """Pull streaming of a scalar set with specular walls: a link whose
         source lies in a wall takes the population that left the mirror node toward the
         wall, i.e. g_k(x) = g*_m(x - (c_kx, 0)) with m the direction (c_kx, -c_ky).
         This is a zero normal flux that keeps the tangential flux of the diagonal links,
@@ -331,7 +331,7 @@ class Oracle:
         bracket = e["ugr"] + cF / CS2 + (cu * cgr - CS2 * e["ugr"]) / CS2
         src_f = _Wf * bracket
 
-        # reaction terms R_phi, R_psi (Sec. 3) with the wall flux of reading c2
+        # reaction terms R_phi, R_psi (Sec. 3) with the kappa-weighted wall flux of the ghost-row closure
         R_phi = d.M_phi * (-4.0 * d.beta * (1.0 - psi) * (phi * phi * phi - phi) - d.W * psi * phi
                            + e["lam"] * e["hp"]) + d.M_phi * d.kappa * (e["LG_phi"] - e["LN_phi"])
         if p.psi_on:
@@ -342,7 +342,7 @@ class Oracle:
             R_psi = np.zeros((ny, nx))
         phiu = np.stack([phi * ux, phi * uy])
         psiu = np.stack([psi * ux, psi * uy])
-        if self.first:   # reading c8: backward differences start from zero
+        if self.first:   # first step: the backward differences start from zero
             self.R_prev_phi, self.R_prev_psi = R_phi, R_psi
             self.phiu_prev, self.psiu_prev = phiu, psiu
         dphiu = phiu - self.phiu_prev

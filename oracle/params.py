@@ -15,7 +15,7 @@ Derivations, each from the paper:
 * nu = c_s^2 (1/s2^1 - 1/2); M_phi kappa = eta_phi c_s^2 (1/s1^2 - 1/2);
   M_psi lambda_s + M_0 = eta_psi c_s^2 (1/s1^3 - 1/2)                   (Sec. 3, relaxation rates)
 
-Readings where the paper is silent (listed in the design doc): M_0 is whatever the
+Readings where the paper is silent: M_0 is whatever the
 last relation leaves once M_psi is chosen; rho and nu interpolate linearly in
 (phi/phi_b + 1)/2; eta_phi = eta_psi = 1 by default; unspecified MRT rates equal
 the field's main rate.
@@ -71,7 +71,7 @@ class OracleParams:
     psi_on: bool = True             # False: surfactant transport disabled, psi == 0
     walls: list = field(default_factory=lambda: [Wall(), Wall()])  # [bottom, top]
     psi_clamp: float = 1e-12
-    saturation: bool = True         # Remark 1 cap: sigma_s,alpha >= sigma_s,alpha,0 / 2 (reading c20)
+    saturation: bool = True         # Remark 1 cap: sigma_s,alpha >= sigma_s,alpha,0 / 2
 
 
 @dataclass

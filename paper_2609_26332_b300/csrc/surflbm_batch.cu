@@ -22,7 +22,7 @@ namespace {
 
 std::string g_batch_create_error = "no error";
 
-// residual of one instance over K steps (reading c17): sums of (x - x_snap)^2 and x^2 for
+// residual of one instance over K steps: sums of (x - x_snap)^2 and x^2 for
 // phi (previous-step phi) and psi (post-collision zeroth moment), then the snapshot update
 struct ResidualArgs {
     const float* php;      // current phi of the instance
@@ -234,7 +234,7 @@ slbm_status run_steps(slbm_batch* b, long long nsteps) {
     return SLBM_OK;
 }
 
-// residual of every active instance (reading c17: max over phi, psi of
+// residual of every active instance (max over phi, psi of
 // ||x^n - x^{n-K}|| / (K ||x^n||)); r[i] = +inf for the first call
 slbm_status residuals(slbm_batch* b, long long K, std::vector<double>& r) {
     r.assign(b->count, INFINITY);

@@ -161,7 +161,7 @@ __device__ __forceinline__ float hprime(float phi, const Phys& P) {
     return __fmul_rn(__fmul_rn(0.75f, P.inv_phi_b), __fsub_rn(1.0f, __fmul_rn(u, u)));
 }
 
-// wetting / adsorption ghost values (Eq. boundary, reading c2): phi_G = phi_w - (df_w/dphi)/kappa,
+// wetting / adsorption ghost values (Eq. boundary, closed by ghost rows): phi_G = phi_w - (df_w/dphi)/kappa,
 // psi_G = psi_w - (df_w/dpsi)/lambda_s, derivatives evaluated at the wall-row values
 __device__ __forceinline__ void wall_ghost(float ph, float ps, int w, const Phys& P, float& phG, float& psG) {
     float psc = P.psi_on ? fminf(fmaxf(ps, P.psi_clamp), 1.0f - P.psi_clamp) : 0.0f;
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
                     ls += Wk(k) * SH(y + CYk(k), pc + CXk(k));
                 });
             } else {
-                // ghost row beyond the wall: Eq. boundary (reading c2), three columns
+                // ghost row beyond the wall: Eq. boundary, three columns
                 const int w = y == 0 ? 0 : 1;
                 const int side = y == 0 ? -1 : 1;
                 float gph[3], gps[3];
@@ -774,7 +774,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
             float Rf;
             ff dR;
             if (s == 0) {
-                // R_phi without the lambda^n term (deferred), with the wall flux of reading c2
+                // R_phi without the lambda^n term (deferred), with the kappa-weighted wall flux of the ghost-row closure
                 Rf = Stor<T>::rnd(P.M_phi * (-4.0f * P.beta * (1.0f - psi) * (phi * phi * phi - phi) -
                                              P.W * psi * phi + P.kappa * wf_phi));
             } else {
