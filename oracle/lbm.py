@@ -184,6 +184,30 @@ class Oracle:
             s = [o[0], main, main, o[1], o[1], o[1], o[2], o[2], o[3]]
         return np.stack(s)
 
+    def _lambda_weight(self):
+        """Weight of R^n in the source 1.5 R^n - 0.5 R^{n-1}; 1 on the first step, where
+        the history starts from R^{-1} := R^0."""
+        return 1.0 if self.first else 1.5
+
+    def _exact_lambda(self, A, B, lam_est):
+        """The root of H(A + lambda B) = H(phi^0) nearest the continuous estimate: a cubic
+        in lambda for the nonlinear constraint (h = 1/2 + g, g cubic in phi), linear for
+        the linear one.  Coefficients are the exact expansion of g(A + lambda B)."""
+        pb = self.d.phi_b
+        if self.p.constraint == "linear":
+            coef = [float(np.sum(B)), float(np.sum(A)) - self.H0]
+        else:
+            k1, k3 = 3.0 / (4.0 * pb), 1.0 / (4.0 * pb ** 3)
+            coef = [float(np.sum(-k3 * B ** 3)),
+                    float(np.sum(-3.0 * k3 * A * B * B)),
+                    float(np.sum(k1 * B - 3.0 * k3 * A * A * B)),
+                    float(np.sum(0.5 + k1 * A - k3 * A ** 3)) - self.H0]
+        roots = np.roots(coef)
+        real = roots[np.abs(roots.imag) <= 1e-9 * np.maximum(1.0, np.abs(roots.real))].real
+        if real.size == 0:
+            raise FloatingPointError("no real multiplier conserves H")
+        return float(real[np.argmin(np.abs(real - lam_est))])
+
     def _collide(self, pop, eq, s, src):
         """pop - M^-1 S M (pop - eq) + M^-1 (I - S/2) M src   (Sec. 3, A^k)."""
         m = np.tensordot(self.Mm, pop - eq, axes=(1, 0)) * s
@@ -357,6 +381,25 @@ class Oracle:
         s_h = self._rates(1.0 / p.tau_h, p.mrt_h, (ny, nx), flow=False)
 
         fpost = self._collide(self.f, feq, s_f, src_f)
+        if p.multiplier == "exact":
+            # phi^{n+1} is affine in lambda^n: the multiplier enters the phi populations
+            # only through w_i a M_phi lambda h' (a = 1.5, or 1 on the first step, where
+            # R^{n-1} := R^n); stream the two parts separately and choose lambda so that
+            # the discrete H(phi^{n+1}) equals H(phi^0) (Sec. 2, the constraint in its
+            # discrete form)
+            a = self._lambda_weight()
+            lam_part = d.M_phi * e["lam"] * e["hp"]
+            R0 = R_phi - lam_part
+            Rp = R0 if self.first else self.R_prev_phi
+            gA = self._stream_scalar(self._collide(self.g, geq, s_g, srcA_g) + _Wf * (1.5 * R0 - 0.5 * Rp))
+            gB = self._stream_scalar(_Wf * (a * d.M_phi * e["hp"]))
+            lam = self._exact_lambda(gA.sum(axis=0), gB.sum(axis=0), e["lam"])
+            e["lam_paper"] = e["lam"]
+            e["lam"] = lam
+            R_phi = R0 + d.M_phi * lam * e["hp"]
+            if self.first:
+                self.R_prev_phi = R_phi
+            gnew = gA + lam * gB
         gpost = self._collide(self.g, geq, s_g, srcA_g) + _Wf * (1.5 * R_phi - 0.5 * self.R_prev_phi)
         if p.psi_on:
             hpost = self._collide(self.h, heq, s_h, srcA_h) + _Wf * (1.5 * R_psi - 0.5 * self.R_prev_psi)
@@ -364,12 +407,13 @@ class Oracle:
             hpost = np.zeros_like(self.h)
 
         self.f = self._stream_flow(fpost, rho)
-        self.g = self._stream_scalar(gpost)
+        self.g = gnew if p.multiplier == "exact" else self._stream_scalar(gpost)
         self.h = self._stream_scalar(hpost)
         self.R_prev_phi, self.R_prev_psi = R_phi, R_psi
         self.phiu_prev, self.psiu_prev = phiu, psiu
         self.first = False
-        self.log.append(dict(n=self.n, lam=e["lam"], mubar=e["mubar"], S1=e["S1"], S2=e["S2"],
+        self.log.append(dict(n=self.n, lam=e["lam"], lam_paper=e.get("lam_paper", e["lam"]),
+                             mubar=e["mubar"], S1=e["S1"], S2=e["S2"],
                              H=e["H"], Q=float(np.sum(2.0 * self._g(phi))), psi_total=float(np.sum(psi)),
                              phi_total=float(np.sum(phi)), kinetic=float(np.sum(0.5 * rho * e["usq"])),
                              clamps=e["clamps"]))

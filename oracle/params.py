@@ -67,7 +67,8 @@ class OracleParams:
     Gx: float = 0.0              # body-force density
     Gy: float = 0.0
     constraint: str = "nonlinear"   # "nonlinear" (h_phi = 1/2 + g) or "linear" (h_phi = phi)
-    multiplier: str = "paper"       # "paper" (Eq. eq15) or "target" (drift-correcting reading)
+    multiplier: str = "paper"       # "paper" (Eq. eq15), "target" (drift-correcting reading) or
+                                    # "exact" (the root of the discrete constraint H(phi^{n+1}) = H(phi^0))
     psi_on: bool = True             # False: surfactant transport disabled, psi == 0
     walls: list = field(default_factory=lambda: [Wall(), Wall()])  # [bottom, top]
     psi_clamp: float = 1e-12
