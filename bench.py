@@ -54,18 +54,21 @@ import numpy as np  # noqa: E402
 from paper_2609_26332_b300 import ranks  # noqa: E402
 
 BYTES_PER_CELL = {"fp32": 264, "fp16": 132, "bf16": 132}   # algorithmic bytes per cell update
+# the exact multiplier's reduction pass reads the phi set's 8 deviation planes, its
+# float-float zeroth moment and phi^n once per cell
+EXACT_BYTES_PER_CELL = {"fp32": 44, "fp16": 28, "bf16": 28}
 
 # DRAM bytes (read + write) per step_kernel launch on the 4096 x 2048 shear workload from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the
 # step kernel's code (comments stripped) and float flags: a changed kernel reports null until re-measured.
-TRAFFIC = {"929333c44eee5d20": {"fp32": 3.14e9, "fp16": 2.10e9, "bf16": 2.10e9}}
+TRAFFIC = {"2169eb268b014efc": {"fp32": 3.14e9, "fp16": 2.10e9, "bf16": 2.10e9}}
 
 
 def kernel_hash():
     import hashlib
     from paper_2609_26332_b300 import build as _b
     h = hashlib.sha256()
-    for f in ("surflbm_step.cuh", "surflbm_device.cuh", "surflbm_api.cu"):
+    for f in ("surflbm_step.cuh", "surflbm_device.cuh"):
         src = open(os.path.join(_b.CSRC, f)).read()
         # code only: comments and layout do not change the kernel the counters were taken on
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
@@ -97,8 +100,9 @@ def init_fields(case):
 
 def make_domain(case, stream):
     from paper_2609_26332_b300 import binding as B
+    mult = {"paper": B.PAPER, "target": B.TARGET, "exact": B.EXACT}[case.get("multiplier", "paper")]
     p = B.default_params(case["nx"], case["ny"], precision=case["precision"], psi_b=case["psi0"],
-                         sigma=SHEAR_SIGMA, Ex=SHEAR_EX, Pi=SHEAR_PI)
+                         sigma=SHEAR_SIGMA, Ex=SHEAR_EX, Pi=SHEAR_PI, multiplier=mult)
     d = B.Domain(p, stream=stream)
     d.set_wall(0, case["theta"], case["beta_sg"], case["beta_sl"], 0.0)
     d.set_wall(1, 90.0, 0.0, 0.0, case["u_w"])
@@ -300,8 +304,8 @@ def run_batch(args, rank, world, dist):
                                       "launches": k_inst * len(specs), "speedup_batched": value / per_inst},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": (TRAFFIC.get(kernel_hash(), {}).get(args.precision)
-                                     if (args.nx, args.ny) == (4096, 2048) else None),
+                         # the batch kernel's DRAM counters were taken on an earlier build
+                         "traffic": None,
                          "peak_kind": peak_kind, "bytes_per_cell": BYTES_PER_CELL[args.precision],
                          "kernel_hash": kernel_hash()},
             "e2e": {"value": world * cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
@@ -480,6 +484,9 @@ def main():
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--ny", type=int, default=2048)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--multiplier", default="paper", choices=["paper", "target", "exact"],
+                    help="lambda_phi of the shear workload: Eq. eq15, its drift-correcting form, or the "
+                         "exact root of the discrete constraint (one extra reduction pass per step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="shear", choices=["shear", "batch", "warmstart", "shear-track", "conv"])
     ap.add_argument("--track-steps", type=int, default=50000)
@@ -519,6 +526,8 @@ def main():
         return
 
     case = shear_case(args.nx, args.ny, args.precision)
+    case["multiplier"] = args.multiplier
+    exact = args.multiplier == "exact"
     cells = args.nx * args.ny
     stream = torch.cuda.current_stream()
     phi0, psi0 = init_fields(case)
@@ -565,7 +574,9 @@ def main():
     if rank == 0:
         peak, peak_kind = measured_peaks()
         per_launch_s = ms_max / 1e3 / args.steps
-        achieved = BYTES_PER_CELL[args.precision] * cells / per_launch_s / 1e9
+        # exact mode: both kernels of the step over the step time
+        bpc = BYTES_PER_CELL[args.precision] + (EXACT_BYTES_PER_CELL[args.precision] if exact else 0)
+        achieved = bpc * cells / per_launch_s / 1e9
         value = world * cells * args.steps / (ms_max / 1e3) / 1e6
         line = {
             "metric": "coupled-step MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
@@ -573,18 +584,21 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
             "data": "synthetic",
             "config": {"workload": f"shear-drop {args.nx}x{args.ny} R={case['R']:.0f} {args.precision} "
-                                   "(512x256 shear configuration scaled to the 4096x2048 target size)",
+                                   "(512x256 shear configuration scaled to the 4096x2048 target size)"
+                                   + (f", {args.multiplier} multiplier" if args.multiplier != "paper" else ""),
                        "nx": args.nx, "ny": args.ny, "cells": cells, "parallelism": f"replicas{world}",
+                       "multiplier": args.multiplier,
                        "l2": "state 2.2 GB >> 126 MB L2, no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": (TRAFFIC.get(kernel_hash(), {}).get(args.precision)
-                                     if (args.nx, args.ny) == (4096, 2048) else None),
-                         "peak_kind": peak_kind, "bytes_per_cell": BYTES_PER_CELL[args.precision],
+                                     if (args.nx, args.ny) == (4096, 2048) and not exact else None),
+                         "peak_kind": peak_kind, "bytes_per_cell": bpc,
+                         "kernels": ["step_kernel"] + (["exact_multiplier_kernel"] if exact else []),
                          "kernel_hash": kernel_hash()},
             "e2e": {"value": world * cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": 16 * cells / args.steps, "d2h_bytes_per_step": 40 * cells / args.steps},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * (2 if exact else 1),
             "clocks": clocks,
             "totals": {"psi_total": tot["psi_total"], "lambda_phi": tot["lambda_phi"],
                        "range_count": tot["range_count"]},

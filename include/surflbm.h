@@ -61,8 +61,14 @@ typedef enum { SLBM_CONSTRAINT_NONLINEAR = 0, SLBM_CONSTRAINT_LINEAR = 1 } slbm_
 
 /* lambda_phi: PAPER = Eq. eq15, lambda = S1 / S2.  TARGET = (S1 + (H0 - H) / M_phi) / S2,
  * which feeds back the discrete drift of H = sum h_phi(phi) away from its initial
- * value H0 (the paper's identity holds for the continuous equation only). */
-typedef enum { SLBM_MULT_PAPER = 0, SLBM_MULT_TARGET = 1 } slbm_multiplier;
+ * value H0 (the paper's identity holds for the continuous equation only).
+ * EXACT = the root, nearest the TARGET value, of H(phi^{n+1}) = H0 for the lattice
+ * field itself (the constraint of Sec. 2 in discrete form): phi^{n+1} is affine in
+ * lambda^n, so this is a cubic (nonlinear constraint) or linear equation whose four
+ * coefficients one extra reduction pass per step sums (about 50 B per cell of reads);
+ * H then stays at H0 up to the FP32 rounding of the per-cell terms.  Single domains
+ * only (slbm_create_batch rejects it). */
+typedef enum { SLBM_MULT_PAPER = 0, SLBM_MULT_TARGET = 1, SLBM_MULT_EXACT = 2 } slbm_multiplier;
 
 typedef struct {
     int nx, ny;              /* grid, nx >= 1, ny >= 2                                  */
@@ -98,7 +104,8 @@ typedef struct {
     double H;                /* sum h_phi(phi): the conserved measure of the constraint */
     double phi_total;        /* sum phi                                                 */
     double psi_total;        /* sum psi (conserved by Eq. AC_psi)                       */
-    double lambda_phi;       /* Lagrange multiplier of Eq. eq15 at this time level      */
+    double lambda_phi;       /* Lagrange multiplier of Eq. eq15 at this time level; in  */
+                             /* EXACT mode after >= 1 step: the root the last step used */
     double mubar_psi;        /* mean surfactant chemical potential (Eq. AC_psi)         */
     double kinetic;          /* sum rho |u|^2 / 2                                       */
     double S1, S2;           /* sum h' mu_phi, sum h'^2                                 */

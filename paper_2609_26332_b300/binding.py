@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_PKG, "libsurflbm.so")
 SLBM_OK, SLBM_EINVAL, SLBM_ENOMEM, SLBM_ECUDA, SLBM_EUNSTABLE, SLBM_ESTATE = range(6)
 FP32, FP16DEV, BF16DEV = 0, 1, 2
 NONLINEAR, LINEAR = 0, 1
-PAPER, TARGET = 0, 1
+PAPER, TARGET, EXACT = 0, 1, 2
 _PREC = {"fp32": FP32, "fp16": FP16DEV, "bf16": BF16DEV}
 
 

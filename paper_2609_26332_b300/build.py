@@ -12,7 +12,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libsurflbm.so")
-SOURCES = ["surflbm_api.cu", "surflbm_batch.cu", "ws_net.cu"]
+SOURCES = ["surflbm_api.cu", "surflbm_batch.cu", "surflbm_exact.cu", "ws_net.cu"]
 HEADERS = ["surflbm_device.cuh", "surflbm_step.cuh", "surflbm_internal.cuh", "ws_tc.cuh", "ws_conv.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP32 denormals flushed, approximate FP32 division and square root: the few divisions and

@@ -105,7 +105,8 @@ std::string validate(const slbm_params* p) {
     if (!(p->eta_phi > 0) || !(p->eta_psi > 0)) return "eta must be positive";
     if (!(p->rho_l > 0) || !(p->rho_g > 0)) return "densities must be positive";
     if (p->constraint != SLBM_CONSTRAINT_NONLINEAR && p->constraint != SLBM_CONSTRAINT_LINEAR) return "bad constraint";
-    if (p->multiplier != SLBM_MULT_PAPER && p->multiplier != SLBM_MULT_TARGET) return "bad multiplier";
+    if (p->multiplier != SLBM_MULT_PAPER && p->multiplier != SLBM_MULT_TARGET && p->multiplier != SLBM_MULT_EXACT)
+        return "bad multiplier";
     if (p->precision < SLBM_FP32 || p->precision > SLBM_BF16DEV) return "bad precision";
     if (p->wall_saturation != 0 && p->wall_saturation != 1) return "wall_saturation must be 0 or 1";
     return "";
@@ -162,7 +163,9 @@ void derive(slbm_domain* d) {
     P.psi_clamp = 1e-12f;
     P.psi_on = p.psi_on != 0;
     P.linear = p.constraint == SLBM_CONSTRAINT_LINEAR;
-    P.target = p.multiplier == SLBM_MULT_TARGET;
+    // the exact root is sought from the target estimate, which also makes the step
+    // kernel reduce H (and so H0 on the first step)
+    P.target = p.multiplier == SLBM_MULT_TARGET || p.multiplier == SLBM_MULT_EXACT;
     P.Nd = (double)p.nx * (double)p.ny;
     P.M_phi_d = d->M_phi;
     P.M_psi_d = p.M_psi;
@@ -466,8 +469,10 @@ slbm_status slbm_step(slbm_domain* d, long long nsteps) {
     if (!d) return SLBM_EINVAL;
     if (nsteps < 0) return fail(d, SLBM_EINVAL, "nsteps must be >= 0");
     if (!d->initialised) return fail(d, SLBM_ESTATE, "fields not initialised");
+    const bool exact = d->p.multiplier == SLBM_MULT_EXACT;
     for (long long s = 0; s < nsteps; ++s) {
         cudaError_t e = launch(d, false);
+        if (e == cudaSuccess && exact) e = launch_exact_multiplier(d);
         if (e != cudaSuccess) return cuda_fail(d, e, "step launch");
         d->cur ^= 1;
         d->n += 1;
@@ -505,6 +510,13 @@ slbm_status slbm_read_totals(slbm_domain* d, slbm_totals* t) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, d->recs + 2, sizeof(Rec), cudaMemcpyDeviceToHost, d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) return cuda_fail(d, e, "read_totals");
+    if (e == cudaSuccess && d->p.multiplier == SLBM_MULT_EXACT && d->n > 0) {
+        Rec last;
+        e = cudaMemcpyAsync(&last, d->recs + ((d->n - 1) & 1), sizeof(Rec), cudaMemcpyDeviceToHost, d->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+        if (e != cudaSuccess) return cuda_fail(d, e, "read_totals");
+        r.lam = last.lam;
+    }
     fill_totals(d, r, t);
     const bool finite = std::isfinite(r.Q) && std::isfinite(r.psi_tot) && std::isfinite(r.lam) && std::isfinite(r.kin);
     if (t->range_count > 0 || !finite) return fail(d, SLBM_EUNSTABLE, "the run has diverged (non-finite or out-of-range values)");
@@ -538,6 +550,13 @@ slbm_status slbm_read_fields_noalloc(slbm_domain* d, double* phi, double* psi, d
                         d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) return cuda_fail(d, e, "read_fields_noalloc");
+    if (e == cudaSuccess && d->p.multiplier == SLBM_MULT_EXACT && d->n > 0) {
+        Rec last;
+        e = cudaMemcpyAsync(&last, d->recs + ((d->n - 1) & 1), sizeof(Rec), cudaMemcpyDeviceToHost, d->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+        if (e != cudaSuccess) return cuda_fail(d, e, "read_totals");
+        r.lam = last.lam;
+    }
     fill_totals(d, r, t);
     const bool finite = std::isfinite(r.Q) && std::isfinite(r.psi_tot) && std::isfinite(r.lam) && std::isfinite(r.kin);
     if (t->range_count > 0 || !finite) return fail(d, SLBM_EUNSTABLE, "the run has diverged (non-finite or out-of-range values)");

@@ -329,6 +329,9 @@ slbm_status slbm_create_batch(const slbm_params* params, const slbm_wall_spec* w
     for (int i = 1; i < count; ++i)
         if (params[i].precision != params[0].precision)
             return bfail(nullptr, SLBM_EINVAL, "all instances of a batch share one precision");
+    for (int i = 0; i < count; ++i)
+        if (params[i].multiplier == SLBM_MULT_EXACT)
+            return bfail(nullptr, SLBM_EINVAL, "the exact multiplier is available for single domains only");
     slbm_batch* b = new (std::nothrow) slbm_batch();
     if (!b) return bfail(nullptr, SLBM_ENOMEM, "host allocation failed");
     b->count = count;

@@ -1,0 +1,144 @@
+// Exact discrete multiplier (the constraint of Sec. 2, H(phi) = sum h_phi(phi), imposed on
+// the lattice field instead of through the continuous projection of Eq. eq15).
+//
+// After step n, phi^{n+1} is affine in lambda^n: the multiplier enters the phi populations
+// only as w_i a M_phi lambda h'(phi^n) (a = 1.5, or 1 on the first step), and the step
+// kernel leaves that term to the next launch, which adds it to each node's zeroth moment
+// before the pull.  So, from the stored post-collision state,
+//     phi^{n+1}(x) = A(x) + lambda B(x),
+//     A = the pull with the term left out (the step kernel's own fixed-point exchange),
+//     B = sum_k w_k a M_phi h'(phi^n(x_k)),  x_k the node the k-th link pulls from
+//         (its mirror across a wall, as in the specular scalar walls),
+// and H(A + lambda B) = H(phi^0) is a cubic in lambda (h = 1/2 + g, g cubic in phi; linear
+// for the linear constraint).  One pass reduces the four coefficients in float-float per
+// thread and FP64 across blocks; the last block takes Newton steps from the step kernel's
+// estimate and overwrites lambda^n in the record of the level, which the next step reads.
+#include "surflbm_internal.cuh"
+
+using namespace slbm;
+
+namespace {
+
+constexpr int EX_THREADS = NTHREADS;
+
+template <class T>
+struct ExactArgs {
+    int nx, ny;
+    long long N;
+    const T* gd;            // deviations of the phi set, planes k = 1..8 (post-collision, step n)
+    const float2* gm;       // its zeroth moments (float-float)
+    const float* php;       // phi^n
+    double* partials;       // [gridDim][NPART]
+    unsigned int* counter;
+    Rec* rec;               // record of level n: in lam (estimate), H0, a; out lam
+    Phys P;
+};
+
+// the fixed-point value node c sends in direction k without the deferred term
+// (the step kernel's stage K with a zero multiplier coefficient)
+template <class T>
+__device__ __forceinline__ int sent_fixed(const ExactArgs<T>& a, long long c, int k, float2 m, float scl) {
+    const float wsc = __fmul_rn(k < 5 ? Wk(1) : Wk(5), scl);
+    return __float2int_rn(__fmaf_rn(Stor<T>::ld(a.gd, (long long)(k - 1) * a.N + c), scl, __fmul_rn(wsc, m.x)));
+}
+
+template <class T>
+__global__ void __launch_bounds__(EX_THREADS) exact_multiplier_kernel(const ExactArgs<T> a) {
+    const Phys& P = a.P;
+    const float scl = (float)(1u << SFIX_PHI), isc = 1.0f / scl;
+    const float coef = (float)(a.rec->a * P.M_phi_d);     // a M_phi
+    ff acc[NPART];
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) acc[q] = {0.0f, 0.0f};
+    const long long stride = (long long)gridDim.x * EX_THREADS;
+    for (long long c = (long long)blockIdx.x * EX_THREADS + threadIdx.x; c < a.N; c += stride) {
+        const int y = (int)(c / a.nx), x = (int)(c - (long long)y * a.nx);
+        const float2 m = a.gm[c];
+        int ksum = 0;
+#pragma unroll
+        for (int k = 1; k < 9; ++k) ksum += sent_fixed(a, c, k, m, scl);
+        int krecv = 0;
+        float bsum = Wk(0) * hprime(a.php[c], P);
+#pragma unroll
+        for (int k = 1; k < 9; ++k) {
+            int sy = y - CYk(k), kk = k;
+            if (sy < 0 || sy >= a.ny) { sy = y; kk = MIRYk(k); }
+            const long long s = (long long)sy * a.nx + wrap1(x - CXk(k), a.nx);
+            krecv += sent_fixed(a, s, kk, a.gm[s], scl);
+            bsum = __fmaf_rn(Wk(k), hprime(a.php[s], P), bsum);
+        }
+        const ff A = ff_add(ff_add({m.x, m.y}, fixed_to_ff(-ksum, isc)), fixed_to_ff(krecv, isc));
+        const float B = coef * bsum;
+        if (P.linear) {
+            acc[0] = ff_add(acc[0], A);
+            acc[1] = ff_add_f(acc[1], B);
+        } else {
+            const float u = (A.hi + A.lo) * P.inv_phi_b, v = B * P.inv_phi_b;
+            // Q(u + lambda v) with Q = (3u - u^3)/2 = 2 g, expanded in lambda
+            acc[0] = ff_add_f(acc[0], 1.5f * u - 0.5f * u * u * u);
+            acc[1] = ff_add_f(acc[1], 1.5f * v * (1.0f - u * u));
+            acc[2] = ff_add_f(acc[2], -1.5f * u * v * v);
+            acc[3] = ff_add_f(acc[3], -0.5f * v * v * v);
+        }
+    }
+
+    __shared__ double s_blk[NPART], s_tot[NPART];
+    __shared__ bool s_last;
+    block_sum(acc, s_blk);
+    if (threadIdx.x < NPART) a.partials[(long long)blockIdx.x * NPART + threadIdx.x] = s_blk[threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    ordered_sum(a.partials, gridDim.x, s_tot);
+    if (threadIdx.x == 0) {
+        Rec* r = a.rec;
+        // target of the cubic: sum Q(phi^0) = 2 H0 - N (nonlinear), sum phi^0 = H0 (linear)
+        const double p0 = s_tot[0] - (P.linear ? r->H0 : 2.0 * r->H0 - P.Nd);
+        const double p1 = s_tot[1], p2 = s_tot[2], p3 = s_tot[3];
+        double lam = r->lam;
+        int it = 0;
+        for (; it < 50; ++it) {      // Newton from the continuous estimate (bounded)
+            const double f = p0 + lam * (p1 + lam * (p2 + lam * p3));
+            const double fp = p1 + lam * (2.0 * p2 + 3.0 * lam * p3);
+            if (!(fp != 0.0)) break;
+            const double dl = f / fp;
+            lam -= dl;
+            if (fabs(dl) <= 1e-15 * fabs(lam)) break;
+        }
+        r->pad[0] = r->lam;          // the estimate the root was started from
+        r->pad[1] = (double)it;
+        if (isfinite(lam)) r->lam = lam;
+        *a.counter = 0u;
+        __threadfence();
+    }
+}
+
+template <class T>
+cudaError_t launch_exact_t(slbm_domain* d) {
+    ExactArgs<T> a;
+    // state after the step just launched: the buffers it wrote
+    const int o = d->cur ^ 1;
+    a.nx = d->p.nx; a.ny = d->p.ny; a.N = d->N;
+    a.gd = (const T*)d->gd[o]; a.gm = d->gm[o]; a.php = d->php[o];
+    a.partials = d->partials;
+    a.counter = d->counter;
+    a.rec = d->recs + (d->n & 1);
+    a.P = d->phys;
+    // the partials buffer holds one slot per CTA of the step grid
+    const int blocks = (int)(d->grid.x * d->grid.y);
+    exact_multiplier_kernel<T><<<blocks, EX_THREADS, 0, d->stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_exact_multiplier(slbm_domain* d) {
+    switch (d->p.precision) {
+        case SLBM_FP16DEV: return launch_exact_t<__half>(d);
+        case SLBM_BF16DEV: return launch_exact_t<__nv_bfloat16>(d);
+        default: return launch_exact_t<float>(d);
+    }
+}

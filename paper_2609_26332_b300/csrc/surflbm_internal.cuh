@@ -33,6 +33,10 @@ struct slbm_domain {
     std::string err = "no error";
 };
 
+// Exact discrete multiplier of the step just queued (surflbm_exact.cu): reduces the
+// coefficients of H(A + lambda B) = H0 and overwrites lambda in the record of that step.
+cudaError_t launch_exact_multiplier(slbm_domain* d);
+
 // A batch of domains stepped by the tile-queue kernel (surflbm_batch.cu).
 struct slbm_batch {
     int count = 0;

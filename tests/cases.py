@@ -55,7 +55,7 @@ def domain_for(c, precision="fp32", stream=None):
     keys = [k for k in BASE if k not in ("constraint", "multiplier", "psi_on")]
     p = B.default_params(c["nx"], c["ny"], precision=precision,
                          constraint=B.LINEAR if c["constraint"] == "linear" else B.NONLINEAR,
-                         multiplier=B.TARGET if c["multiplier"] == "target" else B.PAPER,
+                         multiplier={"paper": B.PAPER, "target": B.TARGET, "exact": B.EXACT}[c["multiplier"]],
                          psi_on=1 if c["psi_on"] else 0, **{k: c[k] for k in keys})
     d = B.Domain(p, stream=stream)
     for w, spec in enumerate(c["walls"]):

@@ -33,7 +33,7 @@ def test_default_params_and_validation():
     p = B.default_params(128, 64)
     assert p.nx == 128 and p.ny == 64 and abs(p.tau_f - 0.8) < 1e-15 and p.psi_on == 1
     for bad in (dict(ny=1), dict(tau_f=0.5), dict(eps=0.0), dict(psi_b=1.0), dict(precision=7),
-                dict(mrt_f=(0, 2.5, 0, 0)), dict(rho_g=-1.0), dict(constraint=3)):
+                dict(mrt_f=(0, 2.5, 0, 0)), dict(rho_g=-1.0), dict(constraint=3), dict(multiplier=3)):
         q = B.default_params(64, 32)
         for k, v in bad.items():
             if k in ("mrt_f",):
@@ -44,6 +44,11 @@ def test_default_params_and_validation():
         with pytest.raises(B.SlbmError) as e:
             B.Domain(q)
         assert e.value.status == B.SLBM_EINVAL
+    # the exact multiplier is a single-domain mode: a batch refuses it before any allocation
+    ok, ex = B.default_params(64, 32), B.default_params(64, 32, multiplier=B.EXACT)
+    with pytest.raises(B.SlbmError) as e:
+        B.Batch([ok, ex])
+    assert e.value.status == B.SLBM_EINVAL and "single domains" in str(e.value)
     # NULL handles are rejected without a crash
     assert B.lib.slbm_step(None, 1) == B.SLBM_EINVAL
     assert B.lib.slbm_set_walls(None, 0, 90.0, 0.0, 0.0, 0.0) == B.SLBM_EINVAL
