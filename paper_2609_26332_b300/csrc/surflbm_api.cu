@@ -392,7 +392,11 @@ slbm_status slbm_create_domain(const slbm_params* p, void* stream, slbm_domain**
         if ((s = dalloc(d, &d->hm[b], N * sizeof(float2)))) break;
         if ((s = dalloc(d, &d->php[b], N * sizeof(float)))) break;
     }
-    const size_t nblocks = (size_t)d->grid.x * d->grid.y;
+    size_t nblocks = (size_t)d->grid.x * d->grid.y;
+    if (p->multiplier == SLBM_MULT_EXACT) {
+        d->exact_blocks = exact_multiplier_blocks(p->precision, d->N);
+        if ((size_t)d->exact_blocks > nblocks) nblocks = (size_t)d->exact_blocks;
+    }
     if (s == SLBM_OK) s = dalloc(d, &d->hist, 6 * N * es);
     if (s == SLBM_OK) s = dalloc(d, &d->partials, nblocks * NPART * sizeof(double));
     if (s == SLBM_OK) s = dalloc(d, &d->counter, sizeof(unsigned int));

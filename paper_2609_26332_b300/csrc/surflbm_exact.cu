@@ -52,20 +52,23 @@ __global__ void __launch_bounds__(EX_THREADS) exact_multiplier_kernel(const Exac
     for (int q = 0; q < NPART; ++q) acc[q] = {0.0f, 0.0f};
     const long long stride = (long long)gridDim.x * EX_THREADS;
     for (long long c = (long long)blockIdx.x * EX_THREADS + threadIdx.x; c < a.N; c += stride) {
-        const int y = (int)(c / a.nx), x = (int)(c - (long long)y * a.nx);
+        // N <= 2^28 (checked at creation): 32-bit index arithmetic
+        const int y = (int)((unsigned)c / (unsigned)a.nx), x = (int)c - y * a.nx;
         const float2 m = a.gm[c];
         int ksum = 0;
 #pragma unroll
         for (int k = 1; k < 9; ++k) ksum += sent_fixed(a, c, k, m, scl);
         int krecv = 0;
-        float bsum = Wk(0) * hprime(a.php[c], P);
+        // h' = 1 for the linear constraint: the term's total is exactly N a M_phi lambda
+        // (the fixed-point exchange telescopes), so its distribution need not be summed
+        float bsum = P.linear ? 1.0f : Wk(0) * hprime(a.php[c], P);
 #pragma unroll
         for (int k = 1; k < 9; ++k) {
             int sy = y - CYk(k), kk = k;
             if (sy < 0 || sy >= a.ny) { sy = y; kk = MIRYk(k); }
             const long long s = (long long)sy * a.nx + wrap1(x - CXk(k), a.nx);
             krecv += sent_fixed(a, s, kk, a.gm[s], scl);
-            bsum = __fmaf_rn(Wk(k), hprime(a.php[s], P), bsum);
+            if (!P.linear) bsum = __fmaf_rn(Wk(k), hprime(a.php[s], P), bsum);
         }
         const ff A = ff_add(ff_add({m.x, m.y}, fixed_to_ff(-ksum, isc)), fixed_to_ff(krecv, isc));
         const float B = coef * bsum;
@@ -127,13 +130,35 @@ cudaError_t launch_exact_t(slbm_domain* d) {
     a.counter = d->counter;
     a.rec = d->recs + (d->n & 1);
     a.P = d->phys;
-    // the partials buffer holds one slot per CTA of the step grid
-    const int blocks = (int)(d->grid.x * d->grid.y);
-    exact_multiplier_kernel<T><<<blocks, EX_THREADS, 0, d->stream>>>(a);
+    // the partials buffer was sized for max(step grid, this grid) at creation
+    exact_multiplier_kernel<T><<<d->exact_blocks, EX_THREADS, 0, d->stream>>>(a);
     return cudaGetLastError();
 }
 
+template <class T>
+int exact_blocks_t(long long N) {
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, exact_multiplier_kernel<T>, EX_THREADS, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const long long need = (N + EX_THREADS - 1) / EX_THREADS;
+    const long long slots = (long long)sms * per_sm;
+    return (int)(need < slots ? (need > 0 ? need : 1) : slots);
+}
+
 }  // namespace
+
+// grid of the reduction pass: every resident slot (the pass is latency-bound: each cell
+// gathers 16 fixed-point values from 9 nodes), at most one CTA per 256 cells
+int exact_multiplier_blocks(int precision, long long N) {
+    switch (precision) {
+        case SLBM_FP16DEV: return exact_blocks_t<__half>(N);
+        case SLBM_BF16DEV: return exact_blocks_t<__nv_bfloat16>(N);
+        default: return exact_blocks_t<float>(N);
+    }
+}
 
 cudaError_t launch_exact_multiplier(slbm_domain* d) {
     switch (d->p.precision) {

@@ -14,6 +14,7 @@ struct slbm_domain {
     double wall_theta[2] = {90.0, 90.0}, wall_bsg[2] = {0, 0}, wall_bsl[2] = {0, 0}, wall_u[2] = {0, 0};
     long long N = 0;
     dim3 grid;
+    int exact_blocks = 0;   // grid of the exact-multiplier pass (EXACT mode only)
     long long total = 0;   // strips * ny, the rows the CTAs share out
     int cur = 0;
     long long n = 0;
@@ -36,6 +37,7 @@ struct slbm_domain {
 // Exact discrete multiplier of the step just queued (surflbm_exact.cu): reduces the
 // coefficients of H(A + lambda B) = H0 and overwrites lambda in the record of that step.
 cudaError_t launch_exact_multiplier(slbm_domain* d);
+int exact_multiplier_blocks(int precision, long long N);
 
 // A batch of domains stepped by the tile-queue kernel (surflbm_batch.cu).
 struct slbm_batch {

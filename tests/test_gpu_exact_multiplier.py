@@ -4,9 +4,12 @@ against the FP64 oracle's exact mode: fields element by element, the root each s
 used, and the conserved measure.
 
 Tolerances: phi, psi 1e-5 max-abs and the root 1e-4 relative, as for the paper's
-multiplier; H to 2e-8 relative -- the per-cell terms of the cubic (and the DIAG sum that
-measures H) are FP32, ~1e-7 relative each, so over N cells the sum carries ~sqrt(N) 1e-7
-absolute, 3e-9 relative at the sizes here."""
+multiplier.  H is held only to the FP32 arithmetic around the root, from two sources:
+the per-cell terms of the cubic (and of the diagnostic sum that measures H) are FP32,
+~2^-24 each and uncorrelated over N cells, and the step applies lambda through an FP32
+coefficient a M_phi lambda, ~2^-24 of the multiplier's total contribution a M_phi |lambda|
+sum h' <= 1.5 M_phi |lambda| N 0.75 / phi_b per step.  Neither accumulates: every step
+re-targets H(phi^0).  The bound allows 8x and 4x of these."""
 import numpy as np
 import pytest
 
@@ -19,6 +22,15 @@ def _cuda():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+
+
+U = 2.0 ** -24
+
+
+def _h_tol(c, lam):
+    o = oracle_for(c)
+    n = c["nx"] * c["ny"]
+    return 8 * np.sqrt(n) * U + 4 * U * 1.5 * o.d.M_phi * abs(lam) * n * 0.75 / o.d.phi_b
 
 
 CASES = [
@@ -48,23 +60,26 @@ def test_exact_multiplier_matches_oracle(c):
     assert np.abs(fg["psi"] - fo["psi"]).max() < 1e-5
     lam_o = o.log[-1]["lam"]
     assert abs(tg["lambda_phi"] - lam_o) <= 1e-4 * abs(lam_o), (tg["lambda_phi"], lam_o)
+    tol = _h_tol(c, lam_o)
     for H in (H_prev, tg["H"]):
-        assert abs(H - H0) <= 2e-8 * H0, (H, H0)
+        assert abs(H - H0) <= tol, (H, H0, tol)
     assert tg["range_count"] == 0
 
 
 def test_paper_multiplier_drifts_where_the_exact_one_does_not():
     _cuda()
     base = CASES[0]
-    drift = {}
+    drift, lam = {}, 0.0
     for mult in ("paper", "exact"):
         c = dict(base, multiplier=mult)
         with domain_for(c) as d:
             H0 = d.read_totals()["H"]
             d.step(300)
-            drift[mult] = abs(d.read_totals()["H"] - H0) / H0
-    assert drift["exact"] < 2e-8
-    assert drift["paper"] > 100 * max(drift["exact"], 1e-10)
+            t = d.read_totals()
+            drift[mult] = abs(t["H"] - H0)
+            lam = t["lambda_phi"]
+    assert drift["exact"] <= _h_tol(base, lam)
+    assert drift["paper"] > 100 * max(drift["exact"], _h_tol(base, lam))
 
 
 def test_linear_constraint_exact_root_is_the_mean_potential():
@@ -80,7 +95,11 @@ def test_linear_constraint_exact_root_is_the_mean_potential():
         d.step(c["steps"])
         t = d.read_totals()
         fg = d.read_fields()
-    assert abs(t["phi_total"] - t0["phi_total"]) <= 1e-12 * abs(t0["phi_total"])
+    # the multiplier's total a M_phi lambda N is applied through one FP32 coefficient
+    M = oracle_for(c).d.M_phi
+    n = c["nx"] * c["ny"]
+    assert abs(t["phi_total"] - t0["phi_total"]) <= 4 * U * 1.5 * M * abs(t["lambda_phi"]) * n + 1e-12 * abs(
+        t0["phi_total"])
     assert np.abs(fg["phi"] - o.fields()["phi"]).max() < 1e-5
     lam_o = o.log[-1]["lam"]
     assert abs(t["lambda_phi"] - lam_o) <= 1e-4 * abs(lam_o)
@@ -96,5 +115,5 @@ def test_exact_multiplier_in_16bit_storage(precision):
         H0 = d.read_totals()["H"]
         d.step(200)
         t = d.read_totals()
-    assert abs(t["H"] - H0) <= 2e-8 * H0
+    assert abs(t["H"] - H0) <= _h_tol(c, t["lambda_phi"])
     assert t["range_count"] == 0
