@@ -20,6 +20,7 @@ using namespace slbm;
 namespace {
 
 constexpr int EX_THREADS = NTHREADS;
+constexpr int EX_TX = 32, EX_TY = EX_THREADS / EX_TX;
 
 template <class T>
 struct ExactArgs {
@@ -50,10 +51,15 @@ __global__ void __launch_bounds__(EX_THREADS) exact_multiplier_kernel(const Exac
     ff acc[NPART];
 #pragma unroll
     for (int q = 0; q < NPART; ++q) acc[q] = {0.0f, 0.0f};
-    const long long stride = (long long)gridDim.x * EX_THREADS;
-    for (long long c = (long long)blockIdx.x * EX_THREADS + threadIdx.x; c < a.N; c += stride) {
-        // N <= 2^28 (checked at creation): 32-bit index arithmetic
-        const int y = (int)((unsigned)c / (unsigned)a.nx), x = (int)c - y * a.nx;
+    // tiles of EX_TX x EX_TY cells, one warp per tile row: the rows y +- 1 a cell gathers
+    // from are mostly the same CTA's rows, still in L1 (N <= 2^28: 32-bit indices)
+    const int ntx = (a.nx + EX_TX - 1) / EX_TX, nty = (a.ny + EX_TY - 1) / EX_TY;
+    const int tx = threadIdx.x % EX_TX, ty = threadIdx.x / EX_TX;
+    for (int t = blockIdx.x; t < ntx * nty; t += gridDim.x) {
+        const int ty0 = t / ntx;
+        const int x = (t - ty0 * ntx) * EX_TX + tx, y = ty0 * EX_TY + ty;
+        if (x >= a.nx || y >= a.ny) continue;
+        const long long c = (long long)y * a.nx + x;
         const float2 m = a.gm[c];
         int ksum = 0;
 #pragma unroll
@@ -143,7 +149,7 @@ int exact_blocks_t(long long N) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, exact_multiplier_kernel<T>, EX_THREADS, 0) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
-    const long long need = (N + EX_THREADS - 1) / EX_THREADS;
+    const long long need = (N + EX_THREADS - 1) / EX_THREADS;   // about the number of tiles
     const long long slots = (long long)sms * per_sm;
     return (int)(need < slots ? (need > 0 ? need : 1) : slots);
 }
