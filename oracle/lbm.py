@@ -312,7 +312,10 @@ class Oracle:
         gpx, gpy = gradient(mpP, ny, nx)
         Fx = -phi * gmx - psi * gpx + p.Gx
         Fy = -phi * gmy - psi * gpy + p.Gy
-        chi = 0.5 * (phi / d.phi_b + 1.0)
+        # liquid fraction, clipped to [0, 1]: the bulk |phi| exceeds phi_b(psi_b) wherever
+        # the bulk surfactant falls below psi_b (Sec. 2.2), and rho, nu stay within the
+        # pure-phase values (at rho_l / rho_g = 1000 an unclipped chi of -1e-3 gives rho ~ 0)
+        chi = np.clip(0.5 * (phi / d.phi_b + 1.0), 0.0, 1.0)
         rho = p.rho_g + (p.rho_l - p.rho_g) * chi
         grx, gry = gradient(_pad(rho, rho[0], rho[-1]), ny, nx)
         f = self.f
