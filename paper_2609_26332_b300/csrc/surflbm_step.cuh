@@ -155,6 +155,12 @@ __device__ __forceinline__ float addc(float acc, int sgn, float v) {
 }
 
 // h_phi'(phi) = g'(phi) = 3/(4 phi_b) (1 - phi^2/phi_b^2), or 1 for the linear constraint
+// liquid fraction of the density / viscosity interpolation, clipped to [0, 1] (the bulk
+// |phi| exceeds phi_b(psi_b) where the bulk surfactant is below psi_b)
+__device__ __forceinline__ float liquid_fraction(float phi, const Phys& P) {
+    return fminf(fmaxf(0.5f * (phi * P.inv_phi_b + 1.0f), 0.0f), 1.0f);
+}
+
 __device__ __forceinline__ float hprime(float phi, const Phys& P) {
     if (P.linear) return 1.0f;
     float u = __fmul_rn(phi, P.inv_phi_b);
@@ -589,7 +595,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
                 f[k] = Stor<T>::ld(fin + (k * (unsigned)N), rowb + sx);
             });
             if (wall_row) {
-                const float rho_w = VARRHO ? P.rho_g + (P.rho_l - P.rho_g) * 0.5f * (php_self * P.inv_phi_b + 1.0f) : P.rho_l;
+                const float rho_w = VARRHO ? P.rho_g + (P.rho_l - P.rho_g) * liquid_fraction(php_self, P) : P.rho_l;
                 static_for<1, 9>([&](auto K) {
                     constexpr int k = decltype(K)::value;
                     constexpr int o = OPPk(k);
@@ -614,8 +620,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
                 gmx = addc(gmx, cx, mu); gmy = addc(gmy, cy, mu);
                 gpx = addc(gpx, cx, mp); gpy = addc(gpy, cy, mp);
                 if (VARRHO) {
-                    const float vphi = w3 * PH(y + cy, pc + cx);
-                    grx = addc(grx, cx, vphi); gry = addc(gry, cy, vphi);
+                    const float vchi = w3 * liquid_fraction(PH(y + cy, pc + cx), P);
+                    grx = addc(grx, cx, vchi); gry = addc(gry, cy, vchi);
                 }
                 lns += Wk(k) * SH(y + cy, pc + cx);
             });
@@ -633,7 +639,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
                 gpx = addc(gpx, cx, mp); gpy = addc(gpy, cy, mp);
                 const float vphi = PH(ym, pc + cx);
                 const float vpsi = SH(ym, pc + cx);
-                if (VARRHO) { grx = addc(grx, cx, w3 * vphi); gry = addc(gry, cy, w3 * vphi); }
+                if (VARRHO) {
+                    const float vchi = w3 * liquid_fraction(vphi, P);
+                    grx = addc(grx, cx, vchi); gry = addc(gry, cy, vchi);
+                }
                 lns += Wk(k) * vpsi;
                 if (out) {
                     float gph, gps;
@@ -649,9 +658,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
         const float Fy = -phi * gmy - psi * gpy + P.Gy;
         float chi = 0.f, rho = P.rho_l, inv_rho = inv_rho_l;
         if (VARRHO) {
-            const float drho = (P.rho_l - P.rho_g) * 0.5f * P.inv_phi_b;
+            // grad rho = (rho_l - rho_g) grad chi over the clipped neighbour values
+            const float drho = P.rho_l - P.rho_g;
             grx *= drho; gry *= drho;
-            chi = 0.5f * (phi * P.inv_phi_b + 1.0f);
+            chi = liquid_fraction(phi, P);
             rho = P.rho_g + (P.rho_l - P.rho_g) * chi;
             inv_rho = __frcp_rn(rho);
         }
