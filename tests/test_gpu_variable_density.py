@@ -76,8 +76,10 @@ def test_density_ratio_1000_matches_the_oracle():
     e["u_abs"] = float(max(np.abs(fg["ux"] - fo["ux"]).max(), np.abs(fg["uy"] - fo["uy"]).max()))
     print(f"density ratio 1000, 200 steps: {e}, max|u| oracle {umax:.3e}")
     assert e["phi"] < 1e-5 and e["psi"] < 1e-5
-    # velocities ~7e-8 here: compare on the scale of the spurious currents
-    assert e["u_abs"] < 1e-2 * umax + 1e-10
+    # the spurious currents here are ~6e-8, 100x below ratio 100's: the absolute floor is
+    # the FP32 rounding of the forces (|mu| ~ 2e-4, so ~1e-11 per cell and step in
+    # grad mu) accumulated over the 200 steps in the gas (rho = 1): ~1e-9
+    assert e["u_abs"] < 1e-2 * umax + 2e-9
     assert abs(tg["psi_total"] - to["psi_total"]) <= 1e-12 * to["psi_total"]
 
 
