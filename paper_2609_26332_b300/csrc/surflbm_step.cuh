@@ -581,6 +581,20 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
         // flow pull first (longest latency): halfway bounce-back with the moving-wall term
         float f[9];
         const float php_self = __ldg(php_in + c);
+        // the source-term history of the previous step, loaded here so that its latency
+        // overlaps the flow part (after the f stores the loads could not move up)
+        T* hi_ = hist + c;
+        float Rp_phi = 0.f, Rp_psi = 0.f, hphux = 0.f, hphuy = 0.f, hpsux = 0.f, hpsuy = 0.f;
+        if (!DIAG && !first) {
+            Rp_phi = Stor<T>::ld(hi_, 0);
+            hphux = Stor<T>::ld(hi_, 2 * N);
+            hphuy = Stor<T>::ld(hi_, 3 * N);
+            if (P.psi_on) {
+                Rp_psi = Stor<T>::ld(hi_, N);
+                hpsux = Stor<T>::ld(hi_, 4 * N);
+                hpsuy = Stor<T>::ld(hi_, 5 * N);
+            }
+        }
         {
             const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
             const T* fin = f_in;
@@ -761,16 +775,13 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
 
         // ---- history of the source terms (Sec. 3, backward differences)
         const float phux = phi * ux, phuy = phi * uy, psux = psi * ux, psuy = psi * uy;
-        float dphux = 0.f, dphuy = 0.f, dpsux = 0.f, dpsuy = 0.f, Rp_phi = 0.f, Rp_psi = 0.f;
-        T* hi_ = hist + c;
+        float dphux = 0.f, dphuy = 0.f, dpsux = 0.f, dpsuy = 0.f;
         if (!first) {
-            Rp_phi = Stor<T>::ld(hi_, 0);
-            dphux = phux - Stor<T>::ld(hi_, 2 * N);
-            dphuy = phuy - Stor<T>::ld(hi_, 3 * N);
+            dphux = phux - hphux;
+            dphuy = phuy - hphuy;
             if (P.psi_on) {
-                Rp_psi = Stor<T>::ld(hi_, N);
-                dpsux = psux - Stor<T>::ld(hi_, 4 * N);
-                dpsuy = psuy - Stor<T>::ld(hi_, 5 * N);
+                dpsux = psux - hpsux;
+                dpsuy = psuy - hpsuy;
             }
         }
 
