@@ -78,6 +78,13 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
+def state_bytes_per_cell(precision):
+    """Resident state: two buffers of 25 population planes, two float-float zeroth moments
+    and phi of the previous step, plus six history planes in place."""
+    es = 4 if precision == "fp32" else 2
+    return 2 * (25 * es + 16 + 4) + 6 * es
+
+
 DTYPE = {"fp32": "f32", "fp16": "f16-storage/f32-compute", "bf16": "bf16-storage/f32-compute"}
 
 
@@ -588,7 +595,8 @@ def main():
                                    + (f", {args.multiplier} multiplier" if args.multiplier != "paper" else ""),
                        "nx": args.nx, "ny": args.ny, "cells": cells, "parallelism": f"replicas{world}",
                        "multiplier": args.multiplier,
-                       "l2": "state 2.2 GB >> 126 MB L2, no flush"},
+                       "l2": f"state {cells * state_bytes_per_cell(args.precision) / 1e9:.2f} GB >> 126 MB L2, "
+                             "no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": (TRAFFIC.get(kernel_hash(), {}).get(args.precision)
