@@ -26,6 +26,11 @@ the median ratio of cold to warm steps to equilibrium.
 Workload 'shear-track': the 512 x 256 shear configuration run to 50,000 steps for three
 solid-gas adsorption strengths (one batch), tracking the wetted segment on the wall.
 
+Workload 'drop1000': a surfactant-laden drop at rest at the paper's density and viscosity
+ratios (1000 and 100) on the same grid: the variable-property specialisation of the
+step.  Option --multiplier exact adds the exact discrete multiplier's reduction pass
+to every step of the shear or drop workload.
+
 Workload 'conv': throughput of the warm-start network's tensor-core convolutions
 (forward, input gradient, weight gradient) on its heaviest layers, against the BF16
 tensor peak.
@@ -99,17 +104,29 @@ def shear_case(nx, ny, precision="fp32"):
                 precision=precision)
 
 
+def drop1000_case(nx, ny, precision="fp32"):
+    """A surfactant-laden drop at rest at the paper's density and viscosity ratios (Sec. 4.2:
+    rho_l / rho_g = 1000, mu_l / mu_g = 100, sigma_gl,0 = 0.001, W = 0.24 and k_B T = 0.162
+    relative to beta, i.e. Ex = 0.5, Pi = 1.35): the variable-property specialisation of the
+    step on the benchmark grid, neutral no-slip walls."""
+    return dict(nx=nx, ny=ny, R=0.25 * ny, xc=nx / 2.0, theta=90.0, psi0=0.01, beta_sg=0.0, beta_sl=0.0, u_w=0.0,
+                precision=precision, init="free", sigma=0.001, rho_l=1000.0, rho_g=1.0, tau_f=0.53, tau_f_gas=0.8)
+
+
 def init_fields(case):
     from paper_2609_26332_b300 import inputs
     pb = inputs.bulk_phi(case["psi0"], SHEAR_EX)
+    if case.get("init") == "free":
+        return inputs.free_drop(case["nx"], case["ny"], case["R"], 4.0, phi_b=pb, psi0=case["psi0"])
     return inputs.sessile_drop(case["nx"], case["ny"], case["R"], 4.0, xc=case["xc"], phi_b=pb, psi0=case["psi0"])
 
 
 def make_domain(case, stream):
     from paper_2609_26332_b300 import binding as B
     mult = {"paper": B.PAPER, "target": B.TARGET, "exact": B.EXACT}[case.get("multiplier", "paper")]
+    extra = {k: case[k] for k in ("rho_l", "rho_g", "tau_f", "tau_f_gas") if k in case}
     p = B.default_params(case["nx"], case["ny"], precision=case["precision"], psi_b=case["psi0"],
-                         sigma=SHEAR_SIGMA, Ex=SHEAR_EX, Pi=SHEAR_PI, multiplier=mult)
+                         sigma=case.get("sigma", SHEAR_SIGMA), Ex=SHEAR_EX, Pi=SHEAR_PI, multiplier=mult, **extra)
     d = B.Domain(p, stream=stream)
     d.set_wall(0, case["theta"], case["beta_sg"], case["beta_sl"], 0.0)
     d.set_wall(1, 90.0, 0.0, 0.0, case["u_w"])
@@ -495,7 +512,8 @@ def main():
                     help="lambda_phi of the shear workload: Eq. eq15, its drift-correcting form, or the "
                          "exact root of the discrete constraint (one extra reduction pass per step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="shear", choices=["shear", "batch", "warmstart", "shear-track", "conv"])
+    ap.add_argument("--workload", default="shear", choices=["shear", "drop1000", "batch", "warmstart", "shear-track",
+                                                             "conv"])
     ap.add_argument("--track-steps", type=int, default=50000)
     ap.add_argument("--ws-train", type=int, default=4096)
     ap.add_argument("--ws-eval", type=int, default=256)
@@ -532,7 +550,7 @@ def main():
             dist.destroy_process_group()
         return
 
-    case = shear_case(args.nx, args.ny, args.precision)
+    case = (drop1000_case if args.workload == "drop1000" else shear_case)(args.nx, args.ny, args.precision)
     case["multiplier"] = args.multiplier
     exact = args.multiplier == "exact"
     cells = args.nx * args.ny
@@ -590,8 +608,11 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
             "data": "synthetic",
-            "config": {"workload": f"shear-drop {args.nx}x{args.ny} R={case['R']:.0f} {args.precision} "
-                                   "(512x256 shear configuration scaled to the 4096x2048 target size)"
+            "config": {"workload": (f"shear-drop {args.nx}x{args.ny} R={case['R']:.0f} {args.precision} "
+                                    "(512x256 shear configuration scaled to the 4096x2048 target size)")
+                                   if args.workload == "shear" else
+                                   (f"surfactant drop at rest {args.nx}x{args.ny} R={case['R']:.0f} {args.precision}, "
+                                    "rho_l/rho_g = 1000, mu_l/mu_g = 100 (variable-property step)")
                                    + (f", {args.multiplier} multiplier" if args.multiplier != "paper" else ""),
                        "nx": args.nx, "ny": args.ny, "cells": cells, "parallelism": f"replicas{world}",
                        "multiplier": args.multiplier,
@@ -600,7 +621,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": (TRAFFIC.get(kernel_hash(), {}).get(args.precision)
-                                     if (args.nx, args.ny) == (4096, 2048) and not exact else None),
+                                     if (args.nx, args.ny) == (4096, 2048) and not exact and args.workload == "shear"
+                                     else None),
                          "peak_kind": peak_kind, "bytes_per_cell": bpc,
                          "kernels": ["step_kernel"] + (["exact_multiplier_kernel"] if exact else []),
                          "kernel_hash": kernel_hash()},
