@@ -608,11 +608,11 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
             "data": "synthetic",
-            "config": {"workload": (f"shear-drop {args.nx}x{args.ny} R={case['R']:.0f} {args.precision} "
-                                    "(512x256 shear configuration scaled to the 4096x2048 target size)")
-                                   if args.workload == "shear" else
-                                   (f"surfactant drop at rest {args.nx}x{args.ny} R={case['R']:.0f} {args.precision}, "
-                                    "rho_l/rho_g = 1000, mu_l/mu_g = 100 (variable-property step)")
+            "config": {"workload": ((f"shear-drop {args.nx}x{args.ny} R={case['R']:.0f} {args.precision} "
+                                     "(512x256 shear configuration scaled to the 4096x2048 target size)")
+                                    if args.workload == "shear" else
+                                    (f"surfactant drop at rest {args.nx}x{args.ny} R={case['R']:.0f} {args.precision}, "
+                                     "rho_l/rho_g = 1000, mu_l/mu_g = 100 (variable-property step)"))
                                    + (f", {args.multiplier} multiplier" if args.multiplier != "paper" else ""),
                        "nx": args.nx, "ny": args.ny, "cells": cells, "parallelism": f"replicas{world}",
                        "multiplier": args.multiplier,
