@@ -65,9 +65,11 @@ typedef enum { SLBM_CONSTRAINT_NONLINEAR = 0, SLBM_CONSTRAINT_LINEAR = 1 } slbm_
  * EXACT = the root, nearest the TARGET value, of H(phi^{n+1}) = H0 for the lattice
  * field itself (the constraint of Sec. 2 in discrete form): phi^{n+1} is affine in
  * lambda^n, so this is a cubic (nonlinear constraint) or linear equation whose four
- * coefficients one extra reduction pass per step sums (about 50 B per cell of reads);
- * H then stays at H0 up to the FP32 rounding of the per-cell terms.  Single domains
- * only (slbm_create_batch rejects it). */
+ * coefficients one extra reduction pass per step sums (44 B per cell of reads with FP32
+ * storage, 28 B with 16-bit); H then stays at H0 up to the FP32 rounding of the per-cell
+ * terms.  If Newton's method finds no root, the step keeps the TARGET value and
+ * slbm_read_totals returns EUNSTABLE.  Single domains only (slbm_create_batch rejects
+ * it). */
 typedef enum { SLBM_MULT_PAPER = 0, SLBM_MULT_TARGET = 1, SLBM_MULT_EXACT = 2 } slbm_multiplier;
 
 typedef struct {

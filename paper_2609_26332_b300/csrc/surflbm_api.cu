@@ -520,6 +520,10 @@ slbm_status slbm_read_totals(slbm_domain* d, slbm_totals* t) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
         if (e != cudaSuccess) return cuda_fail(d, e, "read_totals");
         r.lam = last.lam;
+        if (last.pad[1] < 0.0) {
+            fill_totals(d, r, t);
+            return fail(d, SLBM_EUNSTABLE, "exact multiplier: Newton's method found no root in the last step");
+        }
     }
     fill_totals(d, r, t);
     const bool finite = std::isfinite(r.Q) && std::isfinite(r.psi_tot) && std::isfinite(r.lam) && std::isfinite(r.kin);
@@ -560,6 +564,10 @@ slbm_status slbm_read_fields_noalloc(slbm_domain* d, double* phi, double* psi, d
         if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
         if (e != cudaSuccess) return cuda_fail(d, e, "read_totals");
         r.lam = last.lam;
+        if (last.pad[1] < 0.0) {
+            fill_totals(d, r, t);
+            return fail(d, SLBM_EUNSTABLE, "exact multiplier: Newton's method found no root in the last step");
+        }
     }
     fill_totals(d, r, t);
     const bool finite = std::isfinite(r.Q) && std::isfinite(r.psi_tot) && std::isfinite(r.lam) && std::isfinite(r.kin);

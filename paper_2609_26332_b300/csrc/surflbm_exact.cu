@@ -105,21 +105,28 @@ __global__ void __launch_bounds__(EX_THREADS) exact_multiplier_kernel(const Exac
     if (threadIdx.x == 0) {
         Rec* r = a.rec;
         // target of the cubic: sum Q(phi^0) = 2 H0 - N (nonlinear), sum phi^0 = H0 (linear)
-        const double p0 = s_tot[0] - (P.linear ? r->H0 : 2.0 * r->H0 - P.Nd);
+        const double target = P.linear ? r->H0 : 2.0 * r->H0 - P.Nd;
+        const double p0 = s_tot[0] - target;
         const double p1 = s_tot[1], p2 = s_tot[2], p3 = s_tot[3];
+        // |f| at the rounding level of the difference that makes p0 also counts as a root
+        // (a root at lambda ~ 0 never meets the relative step test)
+        const double f_tol = 1e-14 * (fabs(s_tot[0]) + fabs(target));
         double lam = r->lam;
         int it = 0;
-        for (; it < 50; ++it) {      // Newton from the continuous estimate (bounded)
+        bool converged = !(p1 != 0.0);   // no multiplier term (M_phi = 0): nothing to solve
+        for (; it < 50 && !converged; ++it) {   // Newton from the continuous estimate (bounded)
             const double f = p0 + lam * (p1 + lam * (p2 + lam * p3));
+            if (fabs(f) <= f_tol) { converged = true; break; }
             const double fp = p1 + lam * (2.0 * p2 + 3.0 * lam * p3);
             if (!(fp != 0.0)) break;
             const double dl = f / fp;
             lam -= dl;
-            if (fabs(dl) <= 1e-15 * fabs(lam)) break;
+            converged = fabs(dl) <= 1e-15 * fabs(lam);
         }
         r->pad[0] = r->lam;          // the estimate the root was started from
-        r->pad[1] = (double)it;
-        if (isfinite(lam)) r->lam = lam;
+        // iterations taken, or -1: no root found (the estimate stays)
+        r->pad[1] = (converged && isfinite(lam)) ? (double)it : -1.0;
+        if (converged && isfinite(lam)) r->lam = lam;
         *a.counter = 0u;
         __threadfence();
     }
