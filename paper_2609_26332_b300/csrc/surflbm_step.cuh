@@ -900,11 +900,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
         stagePhi(I4{}, ys - 2);
         __syncthreads();
         stageMu(I2{}, ys - 1);
+        cp_async_wait_all();   // the first iteration's rows
         __syncthreads();
         int b = 1;
         for (int r = ys; r < ye; r += RB) {
-            cp_async_wait_all();
-            __syncthreads();
             if (r + RB < ye) issue(b ^ 1, r + RB + 3, RB);   // next iteration's rows, overlapped
             stageK(I4{}, b, r + 3);
             __syncthreads();
@@ -913,6 +912,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
             stageMu(I4{}, r + 1);
             __syncthreads();
             stageCollide(r, min(r + RB, ye));
+            // one barrier both publishes the next iteration's staged rows and frees the
+            // rings this collide read
+            cp_async_wait_all();
             __syncthreads();
             b ^= 1;
         }
