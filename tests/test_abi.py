@@ -33,7 +33,8 @@ def test_default_params_and_validation():
     p = B.default_params(128, 64)
     assert p.nx == 128 and p.ny == 64 and abs(p.tau_f - 0.8) < 1e-15 and p.psi_on == 1
     for bad in (dict(ny=1), dict(tau_f=0.5), dict(eps=0.0), dict(psi_b=1.0), dict(precision=7),
-                dict(mrt_f=(0, 2.5, 0, 0)), dict(rho_g=-1.0), dict(constraint=3), dict(multiplier=3)):
+                dict(mrt_f=(0, 2.5, 0, 0)), dict(rho_g=-1.0), dict(constraint=3), dict(multiplier=3),
+                dict(nx=1 << 15, ny=1 << 14), dict(nx=0)):
         q = B.default_params(64, 32)
         for k, v in bad.items():
             if k in ("mrt_f",):

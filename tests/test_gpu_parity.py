@@ -96,3 +96,16 @@ def test_surfactant_conservation_gpu():
             d.step(500)
             t = d.read_totals()
             assert abs(t["psi_total"] - t0["psi_total"]) / t0["psi_total"] < 1e-12
+
+
+@pytest.mark.parametrize("nx,ny,R", [(1, 24, 8.0), (5, 2, 1.5), (2, 3, 1.0)])
+def test_degenerate_grids(nx, ny, R):
+    """One periodic column (every x neighbour is the node itself), and channels of two and
+    three rows (every row a wall row, the ghost and mirror rules meeting): element-wise
+    against the oracle after 50 steps, sum psi to 1e-12."""
+    c = make_case(f"deg_{nx}x{ny}", nx, ny, 50, walls=((60.0, 0.0, 0.5, 0.0), (90.0, 0.0, 0.0, 0.0)), R=R)
+    err, fo, fg, to, tg = _compare(c)
+    print(c["name"], err)
+    assert err["phi"] < 1e-5 and err["psi"] < 1e-5
+    assert err["u"] < 1e-4
+    assert abs(tg["psi_total"] - to["psi_total"]) / to["psi_total"] < 1e-12
