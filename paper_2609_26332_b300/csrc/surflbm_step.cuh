@@ -385,41 +385,58 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
     constexpr int VEC = (16 / sizeof(T)) > 4 ? (16 / sizeof(T)) : 4;
 
     // ------------------------------------------------------------------ stages
+    // 16-byte staging path: a staged row is PER_ROW chunks (16 deviation planes, 2 moment
+    // planes, phi_prev); this thread always moves chunks q = tid and tid + NTHREADS of every
+    // row.  Their shared-memory offsets, sources at row 0 and source row strides depend only
+    // on the piece's window, so they are set once per piece (a 16-byte chunk never straddles
+    // the periodic seam: window start and nx are multiples of the elements per chunk, so
+    // each chunk is fetched from its wrapped column).
+    constexpr int CD = (int)(WW * sizeof(T) / 16);    // 16-byte chunks per deviation row
+    constexpr int CM = (int)(WW * sizeof(float2) / 16);
+    constexpr int PER_ROW = 16 * CD + 2 * CM + (int)(WW * sizeof(float) / 16);
+    static_assert(PER_ROW <= 2 * NTHREADS, "two staging chunks per thread and row");
+    const unsigned char* csrc[2] = {nullptr, nullptr};
+    int cdst[2] = {0, 0}, cstride[2] = {0, 0};   // stride 0: no chunk
+    auto prep_chunks = [&]() {
+        const int ws = x0 - WOFF;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            int q = tid + j * NTHREADS;
+            cstride[j] = 0;
+            if (q >= PER_ROW) continue;
+            if (q < 16 * CD) {
+                const int pl = q / CD, ch = q - pl * CD;
+                csrc[j] = (const unsigned char*)((pl < 8 ? gd_in : hd_in) + (long long)(pl & 7) * N +
+                                                 wrap1(ws + ch * (int)(16 / sizeof(T)), nx));
+                cdst[j] = pl * WW * (int)sizeof(T) + ch * 16;
+                cstride[j] = nx * (int)sizeof(T);
+            } else if ((q -= 16 * CD) < 2 * CM) {
+                const int pl = q / CM, ch = q - pl * CM;
+                csrc[j] = (const unsigned char*)((pl == 0 ? gm_in : hm_in) + wrap1(ws + 2 * ch, nx));
+                cdst[j] = (int)ST::D_ROW + pl * WW * (int)sizeof(float2) + ch * 16;
+                cstride[j] = nx * (int)sizeof(float2);
+            } else {
+                q -= 2 * CM;
+                csrc[j] = (const unsigned char*)(php_in + wrap1(ws + 4 * q, nx));
+                cdst[j] = (int)(ST::D_ROW + ST::M_ROW) + q * 16;
+                cstride[j] = nx * (int)sizeof(float);
+            }
+        }
+    };
+
     // staging: raw rows [r0, r0 + nrow) of (16 deviation planes, 2 moment planes, phi_prev)
     // for window columns x0 - WOFF .. x0 - WOFF + WW - 1, into buffer b
     auto issue = [&](int b, int r0, int nrow) {
         unsigned char* base = sStg + (size_t)b * ST::BUF;
         const int ws = x0 - WOFF;
         if (vec) {
-            constexpr int CD = (int)(WW * sizeof(T) / 16);    // 16-byte chunks per deviation row
-            constexpr int CM = (int)(WW * sizeof(float2) / 16);
-            constexpr int CP = (int)(WW * sizeof(float) / 16);
-            constexpr int PER_ROW = 16 * CD + 2 * CM + CP;
-            const int items = nrow * PER_ROW;
-            for (int it = tid; it < items; it += NTHREADS) {
-                const int rr = it / PER_ROW;
-                int q = it - rr * PER_ROW;
+            for (int rr = 0; rr < nrow; ++rr) {
                 const int y = r0 + rr;
                 if (y < 0 || y >= ny) continue;
                 unsigned char* row = base + (size_t)rr * ST::ROW;
-                const long long rowoff = (long long)y * nx;
-                // a 16-byte chunk never straddles the periodic seam (window start and nx are
-                // multiples of the elements per chunk), so each chunk is fetched from its
-                // wrapped column
-                if (q < 16 * CD) {
-                    const int pl = q / CD, ch = q - pl * CD;
-                    const T* src = (pl < 8 ? gd_in : hd_in) + (long long)(pl & 7) * N + rowoff +
-                                   wrap1(ws + ch * (int)(16 / sizeof(T)), nx);
-                    cp_async16(row + (size_t)pl * WW * sizeof(T) + ch * 16, (const unsigned char*)src);
-                } else if ((q -= 16 * CD) < 2 * CM) {
-                    const int pl = q / CM, ch = q - pl * CM;
-                    cp_async16(row + ST::D_ROW + (size_t)pl * WW * sizeof(float2) + ch * 16,
-                               (const unsigned char*)((pl == 0 ? gm_in : hm_in) + rowoff + wrap1(ws + 2 * ch, nx)));
-                } else {
-                    q -= 2 * CM;
-                    cp_async16(row + ST::D_ROW + ST::M_ROW + q * 16,
-                               (const unsigned char*)(php_in + rowoff + wrap1(ws + 4 * q, nx)));
-                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    if (cstride[j]) cp_async16(row + cdst[j], csrc[j] + (long long)y * cstride[j]);
             }
             cp_async_commit();
         } else {
@@ -885,6 +902,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
         ye = y1;
         x0 = strip * TX;
         vec = (nx % VEC == 0) && (nx >= WW);   // seam strips wrap chunk by chunk
+        if (vec) prep_chunks();
         __syncthreads();   // the previous piece's last collide read the rings
         issue(0, ys - 3, 4);
         cp_async_wait_all();
