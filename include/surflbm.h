@@ -146,10 +146,11 @@ slbm_status slbm_init_fields(slbm_domain* d, const double* phi, const double* ps
  * (row-major [ny][nx] doubles); used to start from a state computed on the GPU. */
 slbm_status slbm_init_fields_device(slbm_domain* d, const double* phi, const double* psi);
 
-/* Queues nsteps >= 0 time steps on the domain's stream (asynchronous).  Returns the
- * status of previously completed work only when it is already known (ECUDA on a
- * launch failure); divergence is reported by slbm_read_totals.  ESTATE if the
- * fields were never initialised. */
+/* Queues nsteps >= 0 time steps on the domain's stream (asynchronous): one launch of the
+ * fused step kernel per step, plus the exact multiplier's reduction pass after it when
+ * multiplier = SLBM_MULT_EXACT.  Returns the status of previously completed work only
+ * when it is already known (ECUDA on a launch failure); divergence is reported by
+ * slbm_read_totals.  ESTATE if the fields were never initialised. */
 slbm_status slbm_step(slbm_domain* d, long long nsteps);
 
 /* Computes phi, psi, u_x, u_y and p at the current time level (the moments of the
