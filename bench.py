@@ -69,16 +69,20 @@ EXACT_BYTES_PER_CELL = {"fp32": 44, "fp16": 28, "bf16": 28}
 TRAFFIC = {"0639687a74fedb47": {"fp32": 3.13e9, "fp16": 2.10e9, "bf16": 2.10e9}}
 
 
+def code_only(src):
+    """CUDA source without comments and with whitespace collapsed: comments and layout do
+    not change the kernel the counters were taken on."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def kernel_hash():
     import hashlib
     from paper_2609_26332_b300 import build as _b
     h = hashlib.sha256()
     for f in ("surflbm_step.cuh", "surflbm_device.cuh"):
-        src = open(os.path.join(_b.CSRC, f)).read()
-        # code only: comments and layout do not change the kernel the counters were taken on
-        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
-        src = re.sub(r"//[^\n]*", " ", src)
-        h.update(" ".join(src.split()).encode())
+        h.update(code_only(open(os.path.join(_b.CSRC, f)).read()).encode())
     h.update(" ".join(_b.FLOAT_FLAGS).encode())
     return h.hexdigest()[:16]
 
@@ -119,6 +123,21 @@ def init_fields(case):
     if case.get("init") == "free":
         return inputs.free_drop(case["nx"], case["ny"], case["R"], 4.0, phi_b=pb, psi0=case["psi0"])
     return inputs.sessile_drop(case["nx"], case["ny"], case["R"], 4.0, xc=case["xc"], phi_b=pb, psi0=case["psi0"])
+
+
+def step_config(args, case, world):
+    """The `config` object of the single-domain workloads (both arms report the same)."""
+    cells = args.nx * args.ny
+    workload = ((f"shear-drop {args.nx}x{args.ny} R={case['R']:.0f} {args.precision} "
+                 "(512x256 shear configuration scaled to the 4096x2048 target size)")
+                if args.workload == "shear" else
+                (f"surfactant drop at rest {args.nx}x{args.ny} R={case['R']:.0f} {args.precision}, "
+                 "rho_l/rho_g = 1000, mu_l/mu_g = 100 (variable-property step)"))
+    if args.multiplier != "paper":
+        workload += f", {args.multiplier} multiplier"
+    return {"workload": workload, "nx": args.nx, "ny": args.ny, "cells": cells, "parallelism": f"replicas{world}",
+            "multiplier": args.multiplier,
+            "l2": f"state {cells * state_bytes_per_cell(args.precision) / 1e9:.2f} GB >> 126 MB L2, no flush"}
 
 
 def make_domain(case, stream):
@@ -227,12 +246,13 @@ def run_reference(args, rank, world):
     o.step(args.steps)
     dt = time.perf_counter() - t
     v = 512 * 256 * args.steps / dt / 1e6
-    sample = f"numpy FP64 oracle on the 512x256 shear configuration (bounded sample of the workload), 1 thread"
+    sample = (f"numpy FP64 oracle, {args.steps} steps of the 512x256 shear configuration (a bounded sample of "
+              f"the {args.nx}x{args.ny} workload, the same physics scaled down), 1 thread")
     print(json.dumps({
         "impl": "reference", "metric": "coupled-step MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "shear-drop 512x256 (oracle sample of the 4096x2048 shear workload)"},
+        "config": step_config(args, shear_case(args.nx, args.ny, args.precision), world),
         "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -608,16 +628,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
             "data": "synthetic",
-            "config": {"workload": ((f"shear-drop {args.nx}x{args.ny} R={case['R']:.0f} {args.precision} "
-                                     "(512x256 shear configuration scaled to the 4096x2048 target size)")
-                                    if args.workload == "shear" else
-                                    (f"surfactant drop at rest {args.nx}x{args.ny} R={case['R']:.0f} {args.precision}, "
-                                     "rho_l/rho_g = 1000, mu_l/mu_g = 100 (variable-property step)"))
-                                   + (f", {args.multiplier} multiplier" if args.multiplier != "paper" else ""),
-                       "nx": args.nx, "ny": args.ny, "cells": cells, "parallelism": f"replicas{world}",
-                       "multiplier": args.multiplier,
-                       "l2": f"state {cells * state_bytes_per_cell(args.precision) / 1e9:.2f} GB >> 126 MB L2, "
-                             "no flush"},
+            "config": step_config(args, case, world),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": (TRAFFIC.get(kernel_hash(), {}).get(args.precision)
