@@ -14,6 +14,8 @@ phase-field model for surfactant contact line dynamics with solid adsorption"):
 * ``lattice``  - D2Q9 velocities, weights, the natural-moment MRT basis (Sec. 3)
 * ``lbm``      - the three coupled MRT lattice Boltzmann equations (Sec. 3)
 * ``analysis`` - contact angle, zero-level-set area, free energy (Sec. 4)
+* ``warmstart`` - the warm-start network (convolutions, adjoints, loss) in float64
+* ``mms``      - manufactured-solution convergence harness of the scalar equations (Sec. 4.1)
 
 Pins (tests that tie it to something other than itself) live in
 ``tests/test_oracle_*.py``.  Parts without such a pin are marked "parity unpinned"
