@@ -79,3 +79,52 @@ def test_laplace_pressure_and_bulk_shift():
     assert abs(li["delta"] - eps / (12 * R)) < 0.15 * eps / (12 * R)
     assert abs(li["lam"] - sigma / (2 * R)) < 0.15 * sigma / (2 * R)
     assert abs(li["dp"]) < 0.1 * sigma / R
+
+
+def _isotherm_slab(eps, tau_h, kT_slip=1.0):
+    """Flat periodic interfaces, no gradient penalty on psi (lambda_s = 0), the
+    mobility scaled with eps so that M_psi k_B T (the relaxation rate of psi) is the
+    same at every eps; relaxed until nothing changes."""
+    nx = int(16 * eps)
+    p = OracleParams(nx=nx, ny=2, eps=eps, psi_b=0.005, tau_h=tau_h, lambda_s=0.0, M_psi=0.5 * eps / 4.0)
+    phi0 = inputs.slab(nx, 2, nx / 4, 3 * nx / 4, eps, phi_b=inputs.bulk_phi(0.005, p.Ex))
+    o = Oracle(p, phi0, np.full((2, nx), 0.005))
+    o.d.kT *= kT_slip
+    o.step(int(500 * eps))
+    f = o.fields()
+    phi, psi = f["phi"][0], f["psi"][0]
+    d = derive(p)
+    ib = nx // 2
+    pb, sb = phi[ib], psi[ib]
+    # Sec. 2.2: psi(x) = psi_b / (psi_b + (1 - psi_b) exp(-R / k_B T)) with
+    # R = (phi_b^2 - phi^2) [beta (2 - phi_b^2 - phi^2) + W / 2] at lambda_s = 0
+    R = (pb ** 2 - phi ** 2) * (d.beta * (2.0 - pb ** 2 - phi ** 2) + d.W / 2.0)
+    pred = sb / (sb + (1.0 - sb) * np.exp(-R / d.kT))
+    pointwise = np.abs(psi - pred).max() / psi.max()
+    # the interface concentration at the phi = 0 crossing against the Langmuir isotherm
+    # psi_0 = psi_b / (psi_b + (1 - psi_b) psi_c), psi_c = exp(-R(0) / k_B T)
+    i = np.nonzero((phi[:-1] < 0) & (phi[1:] >= 0))[0][0]
+    t = phi[i] / (phi[i] - phi[i + 1])
+    psi0 = psi[i] + t * (psi[i + 1] - psi[i])
+    R0 = pb ** 2 * (d.beta * (2.0 - pb ** 2) + d.W / 2.0)
+    lang = sb / (sb + (1.0 - sb) * math.exp(-R0 / d.kT))
+    return pointwise, abs(psi0 - lang) / lang
+
+
+def test_langmuir_isotherm_at_zero_gradient_penalty():
+    """Sec. 2.2 (equilibrium analysis after Eq. eq_psib): at equilibrium mu_psi is uniform,
+    which at lambda_s = 0 fixes psi(x) in closed form from phi(x) and the bulk values,
+    and at phi = 0 gives the Langmuir isotherm.  This pins the entropic k_B T ln(psi/(1-psi))
+    term and the adsorption terms -beta (1 - phi^2)^2 + (W/2) phi^2 of mu_psi.
+
+    The lattice diffusion of psi (D = c_s^2 (tau_h - 1/2)) and the stencil Laplacian that
+    the explicit -M_0 Lap psi of R_psi cancels it with differ at O(dx^2) over the ~eps/2 wide
+    adsorption layer, so the check is run near tau_h = 1/2 and converges with eps: the
+    error falls ~10x from eps = 8 to 16 and is below 1.5 % at eps = 16.  A 10 % error in
+    k_B T planted in the oracle moves the profile by ~40 %."""
+    p8, c8 = _isotherm_slab(8.0, 0.51)
+    p16, c16 = _isotherm_slab(16.0, 0.51)
+    assert p16 < 1.5e-2 and c16 < 1.5e-2
+    assert p8 / p16 > 4.0 and c8 / c16 > 4.0
+    slip, _ = _isotherm_slab(8.0, 0.51, kT_slip=1.1)
+    assert slip > 5.0 * p8
