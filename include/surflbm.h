@@ -72,6 +72,18 @@ typedef enum { SLBM_CONSTRAINT_NONLINEAR = 0, SLBM_CONSTRAINT_LINEAR = 1 } slbm_
  * it). */
 typedef enum { SLBM_MULT_PAPER = 0, SLBM_MULT_TARGET = 1, SLBM_MULT_EXACT = 2 } slbm_multiplier;
 
+/* Input staging of the step kernel (same results either way; bit-identical fields).
+ * CPASYNC (default): every thread stages the rows of the next iteration with 16-byte
+ * cp.async copies and the collide loads its flow populations from global memory.
+ * TMA: tensor-memory-access tile copies (cp.async.bulk.tensor) issued by the warps' lane 0s
+ * complete mbarriers: the stage-K rows (single buffer) and the collide's flow rows (double
+ * buffer, one iteration ahead); the periodic-seam columns arrive by cp.async.  Applies to
+ * single domains with nx a multiple of 64 and >= 128 (others use CPASYNC).  On the
+ * 4096 x 2048 benchmark it is slower (764 vs 691 us per step): the kernel is bounded by
+ * DRAM traffic and issue together, and the tile copies of 320-byte rows stall the
+ * issuing warps. */
+typedef enum { SLBM_STAGING_CPASYNC = 0, SLBM_STAGING_TMA = 1 } slbm_staging;
+
 typedef struct {
     int nx, ny;              /* grid, nx >= 1, ny >= 2                                  */
     double tau_f;            /* flow relaxation time of the liquid, 1/s2^1 (> 0.5)       */
@@ -97,6 +109,7 @@ typedef struct {
     int psi_on;              /* 0: surfactant transport disabled (psi == 0)             */
     int wall_saturation;     /* 1: solid tensions capped at half their clean values      */
                              /* (Remark 1; inactive while 1 + beta ln(1 - psi_w) > 1/2)  */
+    int staging;             /* slbm_staging: how the step kernel stages its input rows  */
 } slbm_params;
 
 /* Quantities reduced in FP64 over the whole grid at one time level. */
@@ -113,6 +126,11 @@ typedef struct {
     double S1, S2;           /* sum h' mu_phi, sum h'^2                                 */
     long long clamp_count;   /* cells whose psi was clamped inside ln(psi / (1 - psi))  */
     long long range_count;   /* non-finite values or fixed-point range violations       */
+    double free_energy;      /* discrete E_f of Eq. eq1: cell sums of the bulk densities */
+                             /* with kappa/2 |grad phi|^2, lambda_s/2 |grad psi|^2 (the */
+                             /* isotropic gradient with the wetting ghosts), plus the   */
+                             /* wall energy f_w (Eq. eq8) of both wall rows             */
+    double residual;         /* ||phi^n - phi^{n-1}||_2 / ||phi^n||_2 (0 at step 0)      */
 } slbm_totals;
 
 typedef struct slbm_domain slbm_domain;
@@ -127,6 +145,23 @@ void slbm_default_params(slbm_params* p, int nx, int ny);
  * Errors: EINVAL (bad parameters; message in slbm_last_error(NULL)), ENOMEM, ECUDA.
  * On error *out is set to NULL. */
 slbm_status slbm_create_domain(const slbm_params* p, void* stream, slbm_domain** out);
+
+/* Bytes of caller-owned device workspace a domain with parameters *p needs on the
+ * current device (all state, scratch and the field read-back buffer), rounded up to
+ * 256; 0 if *p is invalid.  The figure depends on the device's SM count (it sizes the
+ * per-CTA reduction scratch), so query it with the device that will run the domain. */
+size_t slbm_workspace_bytes(const slbm_params* p);
+
+/* As slbm_create_domain, but every device buffer of the domain is carved from
+ * `workspace`, `bytes` bytes of device memory the caller owns (e.g. a tensor of a host
+ * framework's caching allocator), 256-byte aligned, at least slbm_workspace_bytes(p).
+ * The library then never allocates or frees device memory for this domain: slbm_destroy
+ * releases only the host-side handle and the workspace stays the caller's (it must
+ * outlive the domain and not be used for anything else meanwhile).
+ * Errors: EINVAL (bad parameters, NULL or unaligned workspace), ENOMEM (workspace
+ * smaller than needed; message states both sizes), ECUDA. */
+slbm_status slbm_create_domain_ext(const slbm_params* p, void* workspace, size_t bytes, void* stream,
+                                   slbm_domain** out);
 
 /* Sets one wall (0 bottom, 1 top): clean contact angle theta0 in degrees (0, 180),
  * solid adsorption elasticities beta_sg, beta_sl >= 0 of Eq. langmuir, and the
@@ -180,7 +215,7 @@ slbm_status slbm_read_totals(slbm_domain* d, slbm_totals* t);
  * queues the work on the stream.
  *
  * Scratch: the per-CTA partial sums, the completion counter and the result record live
- * in one file-scope static device array of SLBM_NOALLOC_SCRATCH_BYTES (about 74 KB),
+ * in one file-scope static device array of SLBM_NOALLOC_SCRATCH_BYTES (about 99 KB),
  * held by every GPU that loads this library until the process exits.  The array holds
  * at most SLBM_NOALLOC_MAX_CTAS CTAs of partials; a domain whose grid is larger is
  * rejected with SLBM_EINVAL (grids here are at most 2 CTAs per SM).  The first call on
@@ -193,7 +228,8 @@ slbm_status slbm_read_totals(slbm_domain* d, slbm_totals* t);
  * Errors: EINVAL (NULL domain, grid too large), ESTATE (fields never initialised),
  * ECUDA, EUNSTABLE (as slbm_read_totals). */
 #define SLBM_NOALLOC_MAX_CTAS 1024
-#define SLBM_NOALLOC_SCRATCH_BYTES (SLBM_NOALLOC_MAX_CTAS * 9 * 8 + 256 + 128)
+#define SLBM_NOALLOC_PARTS 12
+#define SLBM_NOALLOC_SCRATCH_BYTES (SLBM_NOALLOC_MAX_CTAS * SLBM_NOALLOC_PARTS * 8 + 256 + 256)
 slbm_status slbm_read_fields_noalloc(slbm_domain* d, double* phi, double* psi, double* ux, double* uy,
                                      double* p, slbm_totals* totals);
 
@@ -264,6 +300,18 @@ int slbm_batch_active(const slbm_batch* b, int* flags);
 size_t slbm_batch_device_bytes(const slbm_batch* b);
 const char* slbm_batch_last_error(const slbm_batch* b);
 void slbm_batch_destroy(slbm_batch* b);
+
+/* Checkpoint / resume.  slbm_save writes the complete state at the current time level
+ * (parameters, walls, step count, populations, zeroth moments, previous phi, source-term
+ * history and the multiplier records of the last two levels) to a binary file; the
+ * file is specific to this library version.  slbm_load restores such a file into a
+ * domain created with the same parameters (every field of slbm_params equal; the walls
+ * are taken from the file), after which stepping continues exactly as the saved run
+ * would have: N steps, save, load, N steps gives bit-identical fields to 2N steps.
+ * Both synchronise the stream.  Errors: EINVAL (NULL path, unreadable or foreign file,
+ * parameter mismatch, I/O failure), ESTATE (save before initialisation), ECUDA. */
+slbm_status slbm_save(slbm_domain* d, const char* path);
+slbm_status slbm_load(slbm_domain* d, const char* path);
 
 /* Bytes of device memory the domain holds. */
 size_t slbm_device_bytes(const slbm_domain* d);

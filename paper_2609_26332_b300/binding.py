@@ -16,6 +16,7 @@ SLBM_OK, SLBM_EINVAL, SLBM_ENOMEM, SLBM_ECUDA, SLBM_EUNSTABLE, SLBM_ESTATE = ran
 FP32, FP16DEV, BF16DEV = 0, 1, 2
 NONLINEAR, LINEAR = 0, 1
 PAPER, TARGET, EXACT = 0, 1, 2
+CPASYNC, TMA = 0, 1
 _PREC = {"fp32": FP32, "fp16": FP16DEV, "bf16": BF16DEV}
 
 
@@ -37,7 +38,7 @@ class Params(ctypes.Structure):
         ("lambda_s", ctypes.c_double), ("psi_b", ctypes.c_double), ("phi_b", ctypes.c_double),
         ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double), ("Gx", ctypes.c_double), ("Gy", ctypes.c_double),
         ("constraint", ctypes.c_int), ("multiplier", ctypes.c_int), ("precision", ctypes.c_int),
-        ("psi_on", ctypes.c_int), ("wall_saturation", ctypes.c_int),
+        ("psi_on", ctypes.c_int), ("wall_saturation", ctypes.c_int), ("staging", ctypes.c_int),
     ]
 
 
@@ -52,6 +53,7 @@ class Totals(ctypes.Structure):
         ("phi_total", ctypes.c_double), ("psi_total", ctypes.c_double), ("lambda_phi", ctypes.c_double),
         ("mubar_psi", ctypes.c_double), ("kinetic", ctypes.c_double), ("S1", ctypes.c_double),
         ("S2", ctypes.c_double), ("clamp_count", ctypes.c_longlong), ("range_count", ctypes.c_longlong),
+        ("free_energy", ctypes.c_double), ("residual", ctypes.c_double),
     ]
 
 
@@ -73,13 +75,18 @@ def _load():
     L.slbm_read_fields_noalloc.restype = ctypes.c_int
     L.slbm_device_bytes.argtypes = [vp]
     L.slbm_device_bytes.restype = ctypes.c_size_t
+    L.slbm_workspace_bytes.argtypes = [ctypes.POINTER(Params)]
+    L.slbm_workspace_bytes.restype = ctypes.c_size_t
+    L.slbm_create_domain_ext.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+    L.slbm_save.argtypes = [vp, ctypes.c_char_p]
+    L.slbm_load.argtypes = [vp, ctypes.c_char_p]
     L.slbm_destroy.argtypes = [vp]
     L.slbm_destroy.restype = None
     L.slbm_last_error.argtypes = [vp]
     L.slbm_last_error.restype = ctypes.c_char_p
     L.slbm_version.restype = ctypes.c_char_p
     for name in ("slbm_create_domain", "slbm_set_walls", "slbm_init_fields", "slbm_step",
-                 "slbm_read_fields", "slbm_read_totals"):
+                 "slbm_read_fields", "slbm_read_totals", "slbm_create_domain_ext", "slbm_save", "slbm_load"):
         getattr(L, name).restype = ctypes.c_int
     # batches
     L.slbm_create_batch.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(WallSpec), i, vp, ctypes.POINTER(vp)]
@@ -170,16 +177,40 @@ def _stream_handle(stream):
     return ctypes.c_void_p(int(h))
 
 
-class Domain:
-    """One simulation domain living on the current CUDA device."""
+def workspace_bytes(params):
+    """slbm_workspace_bytes: device bytes a domain with these parameters needs (current device)."""
+    return int(lib.slbm_workspace_bytes(ctypes.byref(params)))
 
-    def __init__(self, params, stream=None):
+
+class Domain:
+    """One simulation domain living on the current CUDA device.
+
+    workspace: optional caller-owned device memory (a CUDA tensor, or an (address, bytes)
+    pair) that all of the domain's device buffers are carved from (slbm_create_domain_ext);
+    the caller keeps it alive for the domain's lifetime."""
+
+    def __init__(self, params, stream=None, workspace=None):
         self._h = ctypes.c_void_p()
         self.nx, self.ny = params.nx, params.ny
-        st = lib.slbm_create_domain(ctypes.byref(params), _stream_handle(stream), ctypes.byref(self._h))
+        if workspace is None:
+            st = lib.slbm_create_domain(ctypes.byref(params), _stream_handle(stream), ctypes.byref(self._h))
+        else:
+            if hasattr(workspace, "data_ptr"):
+                addr, nbytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+            else:
+                addr, nbytes = workspace
+            st = lib.slbm_create_domain_ext(ctypes.byref(params), ctypes.c_void_p(int(addr)), ctypes.c_size_t(nbytes),
+                                            _stream_handle(stream), ctypes.byref(self._h))
         if st != SLBM_OK:
             raise SlbmError(st, lib.slbm_last_error(None).decode())
         self.params = params
+        self._workspace = workspace
+
+    def save(self, path):
+        self._check(lib.slbm_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        self._check(lib.slbm_load(self._h, os.fsencode(path)))
 
     def _check(self, st):
         if st != SLBM_OK:

@@ -3,6 +3,8 @@
 #include "surflbm.h"
 #include "surflbm_step.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -109,6 +111,7 @@ std::string validate(const slbm_params* p) {
         return "bad multiplier";
     if (p->precision < SLBM_FP32 || p->precision > SLBM_BF16DEV) return "bad precision";
     if (p->wall_saturation != 0 && p->wall_saturation != 1) return "wall_saturation must be 0 or 1";
+    if (p->staging != SLBM_STAGING_CPASYNC && p->staging != SLBM_STAGING_TMA) return "bad staging";
     return "";
 }
 
@@ -185,6 +188,7 @@ StepArgs<T> make_args(slbm_domain* d, bool diag) {
     a.hist = (T*)d->hist;
     a.partials = d->partials;
     a.counter = d->counter;
+    a.err = d->counter + 1;
     a.rec_prev = d->n == 0 ? d->recs + 3 : d->recs + ((d->n - 1) & 1);
     a.rec_out = diag ? d->recs + 2 : d->recs + (d->n & 1);
     a.first = d->n == 0;
@@ -198,44 +202,68 @@ StepArgs<T> make_args(slbm_domain* d, bool diag) {
 
 template <class T>
 cudaError_t prepare_kernels() {
-    static cudaError_t done = cudaErrorNotReady;
-    if (done == cudaErrorNotReady) {
-        const int sm = (int)smem_bytes<T>();
-        done = cudaFuncSetAttribute(step_kernel<T, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(step_kernel<T, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(step_kernel<T, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(step_kernel<T, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    }
-    return done;
+    static PerDeviceOnce once;
+    return once([] {
+        const int sm = (int)smem_bytes<T>(), st = (int)smem_bytes_tma<T>();
+        const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<T, false, false, false>, attr, sm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, true, false, false>, attr, sm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, false, true, false>, attr, sm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, true, true, false>, attr, sm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, false, false, false, true>, attr, st);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, true, false, false, true>, attr, st);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, false, true, false, true>, attr, st);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, true, true, false, true>, attr, st);
+        return e;
+    });
 }
 
+// one launch of the step (or of its diagnostic pass) with the arguments a
 template <class T>
-cudaError_t launch_step(slbm_domain* d, bool diag) {
+cudaError_t launch_with(slbm_domain* d, const StepArgs<T>& a, bool diag) {
     cudaError_t e = prepare_kernels<T>();
     if (e != cudaSuccess) return e;
-    StepArgs<T> a = make_args<T>(d, diag);
     // uniform density and viscosity (the common case) drop every density-gradient term
     const bool var = a.P.var_nu || a.P.rho_l != a.P.rho_g;
-    const size_t sm = smem_bytes<T>();
-    if (diag) {
-        if (var) step_kernel<T, true, true, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, BatchArgs{});
-        else step_kernel<T, true, false, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, BatchArgs{});
+    const BatchArgs nb{};
+    if (d->tma) {
+        const size_t sm = smem_bytes_tma<T>();
+        const TmaMaps& m = d->maps[d->cur];
+        if (diag) {
+            if (var) step_kernel<T, true, true, false, true><<<d->grid, NTHREADS, sm, d->stream>>>(a, nb, m);
+            else step_kernel<T, true, false, false, true><<<d->grid, NTHREADS, sm, d->stream>>>(a, nb, m);
+        } else {
+            if (var) step_kernel<T, false, true, false, true><<<d->grid, NTHREADS, sm, d->stream>>>(a, nb, m);
+            else step_kernel<T, false, false, false, true><<<d->grid, NTHREADS, sm, d->stream>>>(a, nb, m);
+        }
     } else {
-        if (var) step_kernel<T, false, true, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, BatchArgs{});
-        else step_kernel<T, false, false, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, BatchArgs{});
+        const size_t sm = smem_bytes<T>();
+        static const TmaMaps none{};
+        if (diag) {
+            if (var) step_kernel<T, true, true, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, nb, none);
+            else step_kernel<T, true, false, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, nb, none);
+        } else {
+            if (var) step_kernel<T, false, true, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, nb, none);
+            else step_kernel<T, false, false, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, nb, none);
+        }
     }
     return cudaGetLastError();
 }
 
 template <class T>
-int resident_ctas_per_sm() {
+cudaError_t launch_step(slbm_domain* d, bool diag) {
+    return launch_with<T>(d, make_args<T>(d, diag), diag);
+}
+
+template <class T>
+int resident_ctas_per_sm(bool tma) {
     int n = 0;
     if (prepare_kernels<T>() != cudaSuccess) return 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<T, false, false, false>, NTHREADS, smem_bytes<T>()) != cudaSuccess)
-        return 1;
+    const cudaError_t e = tma ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<T, false, false, false, true>,
+                                                                           NTHREADS, smem_bytes_tma<T>())
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<T, false, false, false>,
+                                                                           NTHREADS, smem_bytes<T>());
+    if (e != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
 
@@ -250,6 +278,70 @@ int choose_ctas(slbm_domain* d, int ctas_per_sm) {
     if (n > slots) n = slots;
     if (n < 1) n = 1;
     return (int)n;
+}
+
+// ---- tensor maps of the TMA staging (driver entry point looked up once, no libcuda link)
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag flag;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(flag, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// a map of rank 2 or 3 over `base` (element bytes es), dims/box innermost first
+bool encode_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+                const cuuint32_t* box, int es) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    return fn(m, dt, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// TMA staging: whole strips (nx a multiple of TX, so that only the two seam strips have
+// window columns outside [0, nx), exactly WOFF of them) and at least two strips
+bool tma_eligible(const slbm_params& p) { return p.staging == SLBM_STAGING_TMA && p.nx % TX == 0 && p.nx >= 2 * TX; }
+
+bool build_maps(slbm_domain* d) {
+    const int es = (int)elem_size(d->p.precision);
+    const cuuint64_t nx = (cuuint64_t)d->p.nx, ny = (cuuint64_t)d->p.ny, N = (cuuint64_t)d->N;
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; ++b) {
+        TmaMaps& m = d->maps[b];
+        std::memset(&m, 0, sizeof(m));
+        {
+            const cuuint64_t dims[3] = {nx, ny, 8}, str[2] = {nx * es, N * es};
+            const cuuint32_t box[3] = {(cuuint32_t)WW, (cuuint32_t)RB, 8};
+            ok = ok && encode_map(&m.dev[0], d->gd[b], 3, dims, str, box, es);
+            ok = ok && encode_map(&m.dev[1], d->hd[b], 3, dims, str, box, es);
+        }
+        {
+            const cuuint64_t dims[2] = {2 * nx, ny}, str[1] = {2 * nx * 4};
+            const cuuint32_t box[2] = {(cuuint32_t)(2 * WW), (cuuint32_t)RB};
+            ok = ok && encode_map(&m.mom[0], d->gm[b], 2, dims, str, box, 4);
+            ok = ok && encode_map(&m.mom[1], d->hm[b], 2, dims, str, box, 4);
+        }
+        {
+            const cuuint64_t dims[2] = {nx, ny}, str[1] = {nx * 4};
+            const cuuint32_t box[2] = {(cuuint32_t)WW, (cuuint32_t)RB};
+            ok = ok && encode_map(&m.php, d->php[b], 2, dims, str, box, 4);
+        }
+        {
+            const cuuint64_t dims[3] = {nx, ny, 9}, str[2] = {nx * es, N * es};
+            const cuuint32_t box[3] = {(cuuint32_t)WW, (cuuint32_t)RB, 1};
+            ok = ok && encode_map(&m.f, d->f[b], 3, dims, str, box, es);
+        }
+    }
+    return ok;
 }
 
 cudaError_t launch(slbm_domain* d, bool diag) {
@@ -278,6 +370,19 @@ cudaError_t launch_init(slbm_domain* d, const double* phi0, const double* psi0) 
 
 template <class P>
 slbm_status dalloc(slbm_domain* d, P** ptr, size_t bytes) {
+    if (d->ext) {
+        // carve from the caller's workspace (ws == nullptr: count only, for slbm_workspace_bytes)
+        const size_t off = (d->ws_off + 255) & ~(size_t)255;
+        if (off + bytes > d->ws_size) {
+            *ptr = nullptr;
+            return fail(d, SLBM_ENOMEM, "workspace too small: need " + std::to_string(off + bytes) + " bytes, have " +
+                                            std::to_string(d->ws_size));
+        }
+        *ptr = d->ws ? (P*)(d->ws + off) : nullptr;
+        d->ws_off = off + bytes;
+        d->bytes += bytes;
+        return SLBM_OK;
+    }
     cudaError_t e = cudaMalloc((void**)ptr, bytes);
     if (e != cudaSuccess) {
         *ptr = nullptr;
@@ -288,8 +393,48 @@ slbm_status dalloc(slbm_domain* d, P** ptr, size_t bytes) {
     return SLBM_OK;
 }
 
+// Grid of the step kernel and the sizes that depend on it (current device).
+void plan_domain(slbm_domain* d) {
+    const slbm_params* p = &d->p;
+    int per_sm = 1;
+    const bool tma = tma_eligible(*p) && encode_fn() != nullptr;
+    switch (p->precision) {
+        case SLBM_FP16DEV: per_sm = resident_ctas_per_sm<__half>(tma); break;
+        case SLBM_BF16DEV: per_sm = resident_ctas_per_sm<__nv_bfloat16>(tma); break;
+        default: per_sm = resident_ctas_per_sm<float>(tma); break;
+    }
+    d->total = (long long)((p->nx + TX - 1) / TX) * p->ny;
+    d->grid = dim3((unsigned)choose_ctas(d, per_sm));
+    if (p->multiplier == SLBM_MULT_EXACT) d->exact_blocks = exact_multiplier_blocks(p->precision, d->N);
+}
+
+// Every device buffer of a domain, in a fixed order (the workspace layout of
+// slbm_create_domain_ext); the 5 N-double field buffer only when with_fields.
+slbm_status alloc_state(slbm_domain* d, bool with_fields) {
+    const size_t es = elem_size(d->p.precision);
+    const size_t N = (size_t)d->N;
+    slbm_status s = SLBM_OK;
+    for (int b = 0; b < 2 && s == SLBM_OK; ++b) {
+        if ((s = dalloc(d, &d->f[b], 9 * N * es))) break;
+        if ((s = dalloc(d, &d->gd[b], 8 * N * es))) break;
+        if ((s = dalloc(d, &d->hd[b], 8 * N * es))) break;
+        if ((s = dalloc(d, &d->gm[b], N * sizeof(float2)))) break;
+        if ((s = dalloc(d, &d->hm[b], N * sizeof(float2)))) break;
+        if ((s = dalloc(d, &d->php[b], N * sizeof(float)))) break;
+    }
+    size_t nblocks = (size_t)d->grid.x * d->grid.y;
+    if ((size_t)d->exact_blocks > nblocks) nblocks = (size_t)d->exact_blocks;
+    if (s == SLBM_OK) s = dalloc(d, &d->hist, 6 * N * es);
+    if (s == SLBM_OK) s = dalloc(d, &d->partials, nblocks * NPART * sizeof(double));
+    if (s == SLBM_OK) s = dalloc(d, &d->counter, 2 * sizeof(unsigned int));
+    if (s == SLBM_OK) s = dalloc(d, &d->recs, 4 * sizeof(Rec));
+    if (s == SLBM_OK && with_fields) s = dalloc(d, &d->fields, 5 * N * sizeof(double));
+    return s;
+}
+
 // ---- scratch of slbm_read_fields_noalloc: static device memory, no allocation
-static_assert(sizeof(Rec) <= 128, "record must fit the scratch tail");
+static_assert(sizeof(Rec) <= 256, "record must fit the scratch tail");
+static_assert(NPART == SLBM_NOALLOC_PARTS, "partial slots of the static scratch");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SLBM_NOALLOC_SCRATCH_BYTES];
 
 // device address of g_noalloc_scratch, looked up once per device with that device current
@@ -313,18 +458,23 @@ cudaError_t noalloc_scratch(unsigned char** out) {
 
 template <class T>
 cudaError_t launch_diag_noalloc(slbm_domain* d, unsigned char* scratch, double* o[5]) {
-    cudaError_t e = prepare_kernels<T>();
-    if (e != cudaSuccess) return e;
     StepArgs<T> a = make_args<T>(d, true);
     a.partials = (double*)scratch;
-    a.counter = (unsigned int*)(scratch + SLBM_NOALLOC_MAX_CTAS * 9 * 8);
-    a.rec_out = (Rec*)(scratch + SLBM_NOALLOC_MAX_CTAS * 9 * 8 + 256);
+    a.counter = (unsigned int*)(scratch + SLBM_NOALLOC_MAX_CTAS * NPART * 8);
+    a.err = a.counter + 1;
+    a.rec_out = (Rec*)(scratch + SLBM_NOALLOC_MAX_CTAS * NPART * 8 + 256);
     a.o_phi = o[0]; a.o_psi = o[1]; a.o_ux = o[2]; a.o_uy = o[3]; a.o_p = o[4];
-    const bool var = a.P.var_nu || a.P.rho_l != a.P.rho_g;
-    const size_t sm = smem_bytes<T>();
-    if (var) step_kernel<T, true, true, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, BatchArgs{});
-    else step_kernel<T, true, false, false><<<d->grid, NTHREADS, sm, d->stream>>>(a, BatchArgs{});
-    return cudaGetLastError();
+    return launch_with<T>(d, a, true);
+}
+
+// the step's error bits (a bounded TMA wait that ran out); call after a stream sync
+slbm_status check_err_word(slbm_domain* d, const unsigned int* word) {
+    unsigned int bits = 0;
+    cudaError_t e = cudaMemcpyAsync(&bits, word, sizeof(bits), cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    if (e != cudaSuccess) return cuda_fail(d, e, "error word");
+    if (bits & ERR_TMA_WAIT) return fail(d, SLBM_ECUDA, "a TMA staging wait of the step ran past its bound");
+    return SLBM_OK;
 }
 
 void fill_totals(const slbm_domain* d, const Rec& r, slbm_totals* t) {
@@ -340,6 +490,8 @@ void fill_totals(const slbm_domain* d, const Rec& r, slbm_totals* t) {
     t->S2 = r.S2;
     t->clamp_count = (long long)r.clamps;
     t->range_count = (long long)r.range;
+    t->free_energy = r.ef;
+    t->residual = r.phi2 > 0.0 ? std::sqrt(r.dphi2 / r.phi2) : 0.0;
 }
 
 }  // namespace
@@ -360,53 +512,35 @@ void slbm_default_params(slbm_params* p, int nx, int ny) {
     p->wall_saturation = 1;
 }
 
-slbm_status slbm_create_domain(const slbm_params* p, void* stream, slbm_domain** out) {
+}  // extern "C"
+
+namespace {
+// ws_bytes == 0 and ws == nullptr: the library allocates; otherwise the caller's workspace
+slbm_status create_common(const slbm_params* p, void* stream, void* ws, size_t ws_bytes, bool ext, slbm_domain** out) {
     if (!out) return fail(nullptr, SLBM_EINVAL, "out is NULL");
     *out = nullptr;
     std::string why = validate(p);
     if (!why.empty()) return fail(nullptr, SLBM_EINVAL, why);
+    if (ext && !ws) return fail(nullptr, SLBM_EINVAL, "workspace is NULL");
+    if (ext && ((uintptr_t)ws & 255)) return fail(nullptr, SLBM_EINVAL, "workspace must be 256-byte aligned");
     slbm_domain* d = new (std::nothrow) slbm_domain();
     if (!d) return fail(nullptr, SLBM_ENOMEM, "host allocation failed");
     d->p = *p;
     d->stream = (cudaStream_t)stream;
     d->N = (long long)p->nx * p->ny;
+    d->ext = ext;
+    d->ws = (unsigned char*)ws;
+    d->ws_size = ws_bytes;
     derive(d);
-    {
-        int per_sm = 1;
-        switch (p->precision) {
-            case SLBM_FP16DEV: per_sm = resident_ctas_per_sm<__half>(); break;
-            case SLBM_BF16DEV: per_sm = resident_ctas_per_sm<__nv_bfloat16>(); break;
-            default: per_sm = resident_ctas_per_sm<float>(); break;
-        }
-        d->total = (long long)((p->nx + TX - 1) / TX) * p->ny;
-        d->grid = dim3((unsigned)choose_ctas(d, per_sm));
-    }
-    const size_t es = elem_size(p->precision);
-    const size_t N = (size_t)d->N;
-    slbm_status s = SLBM_OK;
-    for (int b = 0; b < 2 && s == SLBM_OK; ++b) {
-        if ((s = dalloc(d, &d->f[b], 9 * N * es))) break;
-        if ((s = dalloc(d, &d->gd[b], 8 * N * es))) break;
-        if ((s = dalloc(d, &d->hd[b], 8 * N * es))) break;
-        if ((s = dalloc(d, &d->gm[b], N * sizeof(float2)))) break;
-        if ((s = dalloc(d, &d->hm[b], N * sizeof(float2)))) break;
-        if ((s = dalloc(d, &d->php[b], N * sizeof(float)))) break;
-    }
-    size_t nblocks = (size_t)d->grid.x * d->grid.y;
-    if (p->multiplier == SLBM_MULT_EXACT) {
-        d->exact_blocks = exact_multiplier_blocks(p->precision, d->N);
-        if ((size_t)d->exact_blocks > nblocks) nblocks = (size_t)d->exact_blocks;
-    }
-    if (s == SLBM_OK) s = dalloc(d, &d->hist, 6 * N * es);
-    if (s == SLBM_OK) s = dalloc(d, &d->partials, nblocks * NPART * sizeof(double));
-    if (s == SLBM_OK) s = dalloc(d, &d->counter, sizeof(unsigned int));
-    if (s == SLBM_OK) s = dalloc(d, &d->recs, 4 * sizeof(Rec));
+    plan_domain(d);
+    slbm_status s = alloc_state(d, ext);
     if (s != SLBM_OK) {
         g_create_error = d->err;
         slbm_destroy(d);
         return s;
     }
-    cudaError_t e = cudaMemsetAsync(d->counter, 0, sizeof(unsigned int), d->stream);
+    d->tma = tma_eligible(d->p) && build_maps(d);
+    cudaError_t e = cudaMemsetAsync(d->counter, 0, 2 * sizeof(unsigned int), d->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d->recs, 0, 4 * sizeof(Rec), d->stream);
     if (e != cudaSuccess) {
         cuda_fail(nullptr, e, "cudaMemsetAsync");
@@ -415,6 +549,30 @@ slbm_status slbm_create_domain(const slbm_params* p, void* stream, slbm_domain**
     }
     *out = d;
     return SLBM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+slbm_status slbm_create_domain(const slbm_params* p, void* stream, slbm_domain** out) {
+    return create_common(p, stream, nullptr, 0, false, out);
+}
+
+size_t slbm_workspace_bytes(const slbm_params* p) {
+    if (!validate(p).empty()) return 0;
+    slbm_domain d;
+    d.p = *p;
+    d.N = (long long)p->nx * p->ny;
+    d.ext = true;              // count only: ws stays NULL
+    d.ws_size = ~(size_t)0;
+    plan_domain(&d);
+    if (alloc_state(&d, true) != SLBM_OK) return 0;
+    return (d.ws_off + 255) & ~(size_t)255;
+}
+
+slbm_status slbm_create_domain_ext(const slbm_params* p, void* workspace, size_t bytes, void* stream,
+                                   slbm_domain** out) {
+    return create_common(p, stream, workspace, bytes, true, out);
 }
 
 slbm_status slbm_set_walls(slbm_domain* d, int wall, double theta0_deg, double beta_sg, double beta_sl, double u_x) {
@@ -453,7 +611,7 @@ slbm_status init_fields_from(slbm_domain* d, const double* phi, const double* ps
         default: e = launch_init<float>(d, d->fields, d->fields + d->N); break;
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d->recs, 0, 4 * sizeof(Rec), d->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d->counter, 0, sizeof(unsigned int), d->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d->counter, 0, 2 * sizeof(unsigned int), d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);   // host arrays may be freed on return
     if (e != cudaSuccess) return cuda_fail(d, e, "init");
     d->initialised = true;
@@ -514,6 +672,7 @@ slbm_status slbm_read_totals(slbm_domain* d, slbm_totals* t) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, d->recs + 2, sizeof(Rec), cudaMemcpyDeviceToHost, d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) return cuda_fail(d, e, "read_totals");
+    if (slbm_status es = check_err_word(d, d->counter + 1)) return es;
     if (e == cudaSuccess && d->p.multiplier == SLBM_MULT_EXACT && d->n > 0) {
         Rec last;
         e = cudaMemcpyAsync(&last, d->recs + ((d->n - 1) & 1), sizeof(Rec), cudaMemcpyDeviceToHost, d->stream);
@@ -542,7 +701,7 @@ slbm_status slbm_read_fields_noalloc(slbm_domain* d, double* phi, double* psi, d
     cudaError_t e = noalloc_scratch(&scratch);
     if (e != cudaSuccess) return cuda_fail(d, e, "cudaGetSymbolAddress (noalloc scratch)");
     // the completion counter must start at zero
-    e = cudaMemsetAsync(scratch + SLBM_NOALLOC_MAX_CTAS * 9 * 8, 0, sizeof(unsigned int), d->stream);
+    e = cudaMemsetAsync(scratch + SLBM_NOALLOC_MAX_CTAS * NPART * 8, 0, 2 * sizeof(unsigned int), d->stream);
     double* o[5] = {phi, psi, ux, uy, p};
     if (e == cudaSuccess) {
         switch (d->p.precision) {
@@ -554,10 +713,12 @@ slbm_status slbm_read_fields_noalloc(slbm_domain* d, double* phi, double* psi, d
     if (e != cudaSuccess) return cuda_fail(d, e, "read_fields_noalloc");
     if (!t) return SLBM_OK;
     Rec r;
-    e = cudaMemcpyAsync(&r, scratch + SLBM_NOALLOC_MAX_CTAS * 9 * 8 + 256, sizeof(Rec), cudaMemcpyDeviceToHost,
+    e = cudaMemcpyAsync(&r, scratch + SLBM_NOALLOC_MAX_CTAS * NPART * 8 + 256, sizeof(Rec), cudaMemcpyDeviceToHost,
                         d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) return cuda_fail(d, e, "read_fields_noalloc");
+    if (slbm_status es = check_err_word(d, (const unsigned int*)(scratch + SLBM_NOALLOC_MAX_CTAS * NPART * 8) + 1)) return es;
+    if (slbm_status es = check_err_word(d, d->counter + 1)) return es;
     if (e == cudaSuccess && d->p.multiplier == SLBM_MULT_EXACT && d->n > 0) {
         Rec last;
         e = cudaMemcpyAsync(&last, d->recs + ((d->n - 1) & 1), sizeof(Rec), cudaMemcpyDeviceToHost, d->stream);
@@ -575,10 +736,162 @@ slbm_status slbm_read_fields_noalloc(slbm_domain* d, double* phi, double* psi, d
     return SLBM_OK;
 }
 
+// ---- checkpoints: a fixed header, then the current state buffers in a fixed order
+}  // extern "C"
+
+namespace {
+struct CkptHeader {
+    char magic[8];            // "SLBMCKP1"
+    uint32_t version, header_bytes;
+    slbm_params p;
+    double walls[2][4];       // theta0, beta_sg, beta_sl, u_x per wall
+    long long n;
+    unsigned long long N, payload_bytes;
+    uint32_t elem, rec_bytes;
+};
+
+// the device buffers of the current time level, in file order
+int state_planes(slbm_domain* d, void** ptr, size_t* bytes) {
+    const size_t es = elem_size(d->p.precision), N = (size_t)d->N;
+    const int c = d->cur;
+    void* pp[] = {d->f[c], d->gd[c], d->hd[c], d->gm[c], d->hm[c], d->php[c], d->hist, d->recs};
+    const size_t bb[] = {9 * N * es, 8 * N * es, 8 * N * es, N * sizeof(float2), N * sizeof(float2), N * sizeof(float),
+                         6 * N * es, 4 * sizeof(Rec)};
+    for (int i = 0; i < 8; ++i) { ptr[i] = pp[i]; bytes[i] = bb[i]; }
+    return 8;
+}
+
+bool same_params(const slbm_params& a, const slbm_params& b) {
+    const double da[] = {a.tau_f, a.tau_f_gas, a.tau_g, a.tau_h, a.sigma, a.eps, a.Ex, a.Pi, a.M_phi, a.M_psi,
+                         a.eta_phi, a.eta_psi, a.lambda_s, a.psi_b, a.phi_b, a.rho_l, a.rho_g, a.Gx, a.Gy};
+    const double db[] = {b.tau_f, b.tau_f_gas, b.tau_g, b.tau_h, b.sigma, b.eps, b.Ex, b.Pi, b.M_phi, b.M_psi,
+                         b.eta_phi, b.eta_psi, b.lambda_s, b.psi_b, b.phi_b, b.rho_l, b.rho_g, b.Gx, b.Gy};
+    for (size_t i = 0; i < sizeof(da) / sizeof(da[0]); ++i)
+        if (std::memcmp(&da[i], &db[i], sizeof(double))) return false;
+    for (int i = 0; i < 4; ++i)
+        if (a.mrt_f[i] != b.mrt_f[i] || a.mrt_g[i] != b.mrt_g[i] || a.mrt_h[i] != b.mrt_h[i]) return false;
+    return a.nx == b.nx && a.ny == b.ny && a.constraint == b.constraint && a.multiplier == b.multiplier &&
+           a.precision == b.precision && a.psi_on == b.psi_on && a.wall_saturation == b.wall_saturation;
+}
+}  // namespace
+
+extern "C" {
+
+slbm_status slbm_save(slbm_domain* d, const char* path) {
+    if (!d) return SLBM_EINVAL;
+    if (!path) return fail(d, SLBM_EINVAL, "path is NULL");
+    if (!d->initialised) return fail(d, SLBM_ESTATE, "fields not initialised");
+    void* ptr[8];
+    size_t bytes[8];
+    const int np = state_planes(d, ptr, bytes);
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "SLBMCKP1", 8);
+    h.version = 1;
+    h.header_bytes = sizeof(CkptHeader);
+    h.p = d->p;
+    for (int w = 0; w < 2; ++w) {
+        h.walls[w][0] = d->wall_theta[w]; h.walls[w][1] = d->wall_bsg[w];
+        h.walls[w][2] = d->wall_bsl[w]; h.walls[w][3] = d->wall_u[w];
+    }
+    h.n = d->n;
+    h.N = (unsigned long long)d->N;
+    h.elem = (uint32_t)elem_size(d->p.precision);
+    h.rec_bytes = sizeof(Rec);
+    for (int i = 0; i < np; ++i) h.payload_bytes += bytes[i];
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(d, SLBM_EINVAL, std::string("cannot open ") + path + " for writing");
+    bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1;
+    std::string buf;
+    for (int i = 0; i < np && ok; ++i) {
+        buf.resize(bytes[i]);
+        cudaError_t e = cudaMemcpyAsync(&buf[0], ptr[i], bytes[i], cudaMemcpyDeviceToHost, d->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+        if (e != cudaSuccess) {
+            std::fclose(fp);
+            return cuda_fail(d, e, "save");
+        }
+        ok = std::fwrite(buf.data(), 1, bytes[i], fp) == bytes[i];
+    }
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return fail(d, SLBM_EINVAL, std::string("write to ") + path + " failed");
+    return SLBM_OK;
+}
+
+slbm_status slbm_load(slbm_domain* d, const char* path) {
+    if (!d) return SLBM_EINVAL;
+    if (!path) return fail(d, SLBM_EINVAL, "path is NULL");
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(d, SLBM_EINVAL, std::string("cannot open ") + path);
+    CkptHeader h;
+    if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, "SLBMCKP1", 8) != 0 || h.version != 1 ||
+        h.header_bytes != sizeof(CkptHeader)) {
+        std::fclose(fp);
+        return fail(d, SLBM_EINVAL, std::string(path) + " is not a checkpoint of this library version");
+    }
+    if (!same_params(h.p, d->p) || h.N != (unsigned long long)d->N || h.elem != elem_size(d->p.precision) ||
+        h.rec_bytes != sizeof(Rec)) {
+        std::fclose(fp);
+        return fail(d, SLBM_EINVAL, "checkpoint parameters differ from the domain's");
+    }
+    d->cur = 0;
+    void* ptr[8];
+    size_t bytes[8];
+    const int np = state_planes(d, ptr, bytes);
+    size_t total = 0;
+    for (int i = 0; i < np; ++i) total += bytes[i];
+    if (total != h.payload_bytes) {
+        std::fclose(fp);
+        return fail(d, SLBM_EINVAL, "checkpoint payload size mismatch");
+    }
+    std::string buf;
+    for (int i = 0; i < np; ++i) {
+        buf.resize(bytes[i]);
+        if (std::fread(&buf[0], 1, bytes[i], fp) != bytes[i]) {
+            std::fclose(fp);
+            return fail(d, SLBM_EINVAL, std::string(path) + " is truncated");
+        }
+        cudaError_t e = cudaMemcpyAsync(ptr[i], buf.data(), bytes[i], cudaMemcpyHostToDevice, d->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);   // buf is reused
+        if (e != cudaSuccess) {
+            std::fclose(fp);
+            return cuda_fail(d, e, "load");
+        }
+    }
+    std::fclose(fp);
+    for (int w = 0; w < 2; ++w) {
+        d->wall_theta[w] = h.walls[w][0]; d->wall_bsg[w] = h.walls[w][1];
+        d->wall_bsl[w] = h.walls[w][2]; d->wall_u[w] = h.walls[w][3];
+        set_wall_phys(d, w);
+    }
+    d->n = h.n;
+    cudaError_t e = cudaMemsetAsync(d->counter, 0, 2 * sizeof(unsigned int), d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    if (e != cudaSuccess) return cuda_fail(d, e, "load");
+    d->initialised = true;
+    return SLBM_OK;
+}
+
 size_t slbm_device_bytes(const slbm_domain* d) { return d ? d->bytes : 0; }
+
+}  // extern "C"
+
+// Library-internal: the diagnostic pass of the current level written into the domain's own
+// field buffer, reduced with its own partials (no shared scratch); queued on its stream.
+slbm_status diag_into_fields(slbm_domain* d) {
+    if (!d->initialised || !d->fields) return fail(d, SLBM_ESTATE, "fields not initialised");
+    cudaError_t e = launch(d, true);
+    return e == cudaSuccess ? SLBM_OK : cuda_fail(d, e, "diagnostic pass");
+}
+
+extern "C" {
 
 void slbm_destroy(slbm_domain* d) {
     if (!d) return;
+    if (d->ext) {   // the workspace belongs to the caller
+        delete d;
+        return;
+    }
     for (int b = 0; b < 2; ++b) {
         cudaFree(d->f[b]); cudaFree(d->gd[b]); cudaFree(d->hd[b]);
         cudaFree(d->gm[b]); cudaFree(d->hm[b]); cudaFree(d->php[b]);

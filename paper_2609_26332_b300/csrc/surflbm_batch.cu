@@ -57,14 +57,14 @@ __global__ void residual_kernel(const ResidualArgs* args, const int* blk_inst, c
 
 template <class T>
 cudaError_t prepare_batch_kernels() {
-    static cudaError_t done = cudaErrorNotReady;
-    if (done == cudaErrorNotReady) {
+    static PerDeviceOnce once;
+    return once([] {
         const int sm = (int)smem_bytes<T>();
-        done = cudaFuncSetAttribute(step_kernel<T, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (done == cudaSuccess)
-            done = cudaFuncSetAttribute(step_kernel<T, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    }
-    return done;
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<T, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_kernel<T, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        return e;
+    });
 }
 
 }  // namespace
@@ -172,8 +172,9 @@ cudaError_t launch_batch(slbm_batch* b) {
     ba.done = b->d_queue + 1;
     ba.G = b->d_G;
     const size_t sm = smem_bytes<T>();
-    if (b->var) step_kernel<T, false, true, true><<<b->nctas, NTHREADS, sm, b->stream>>>(a, ba);
-    else step_kernel<T, false, false, true><<<b->nctas, NTHREADS, sm, b->stream>>>(a, ba);
+    static const TmaMaps none{};
+    if (b->var) step_kernel<T, false, true, true><<<b->nctas, NTHREADS, sm, b->stream>>>(a, ba, none);
+    else step_kernel<T, false, false, true><<<b->nctas, NTHREADS, sm, b->stream>>>(a, ba, none);
     return cudaGetLastError();
 }
 

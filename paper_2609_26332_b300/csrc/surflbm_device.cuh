@@ -16,8 +16,30 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <mutex>
 
 namespace slbm {
+
+// Host: runs setup() once per device (with that device current) and caches its result;
+// kernel attributes such as the dynamic shared-memory opt-in are per device.  Thread-safe.
+struct PerDeviceOnce {
+    std::mutex mtx;
+    bool done[128] = {};
+    cudaError_t result[128] = {};
+    template <class F>
+    cudaError_t operator()(F&& setup) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lock(mtx);
+        if (!done[dev]) {
+            result[dev] = setup();
+            done[dev] = true;
+        }
+        return result[dev];
+    }
+};
 
 __host__ __device__ constexpr int CXk(int k) { return (k == 1 || k == 5 || k == 8) ? 1 : ((k == 3 || k == 6 || k == 7) ? -1 : 0); }
 __host__ __device__ constexpr int CYk(int k) { return (k == 2 || k == 5 || k == 6) ? 1 : ((k == 4 || k == 7 || k == 8) ? -1 : 0); }

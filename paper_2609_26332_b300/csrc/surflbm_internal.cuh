@@ -27,12 +27,23 @@ struct slbm_domain {
     float* php[2] = {nullptr, nullptr};
     void* hist = nullptr;
     double* partials = nullptr;
-    unsigned int* counter = nullptr;
+    unsigned int* counter = nullptr;   // [0]: CTAs done in the current launch, [1]: error bits (ERR_*)
     slbm::Rec* recs = nullptr;  // [0], [1]: ring by step parity; [2]: diagnostic level; [3]: zeros
     double* fields = nullptr;   // 5 N doubles, allocated on first read
     size_t bytes = 0;
+    // caller-owned device workspace (slbm_create_domain_ext): every buffer is carved from
+    // it in the order of slbm_workspace_bytes and nothing is allocated or freed
+    bool tma = false;                 // the step stages through TMA boxes (maps of both sides)
+    slbm::TmaMaps maps[2];
+    bool ext = false;
+    unsigned char* ws = nullptr;
+    size_t ws_size = 0, ws_off = 0;
     std::string err = "no error";
 };
+
+// The diagnostic pass of the current level into d->fields (phi, psi, ux, uy, p planes),
+// reduced with the domain's own partials; queued on the domain's stream.
+slbm_status diag_into_fields(slbm_domain* d);
 
 // Exact discrete multiplier of the step just queued (surflbm_exact.cu): reduces the
 // coefficients of H(A + lambda B) = H0 and overwrites lambda in the record of that step.

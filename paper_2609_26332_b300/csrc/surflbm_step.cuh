@@ -20,6 +20,7 @@
 // moment, so the next launch applies it when it pulls (a deferred correction,
 // algebraically identical to applying it in this step) and no grid-wide barrier is needed.
 #pragma once
+#include <cuda.h>   // CUtensorMap (type only; maps are encoded through the runtime's driver entry point)
 #include <type_traits>
 #include "surflbm_device.cuh"
 
@@ -32,7 +33,7 @@ constexpr int RING = 8;          // ring depth (rows)
 constexpr int KX = TX + 6;       // columns of the fixed-point ring (3-node halo)
 constexpr int PX = TX + 4;       // columns of the phi / psi ring (2-node halo)
 constexpr int MX = TX + 2;       // columns of the mu ring (1-node halo)
-constexpr int NPART = 9;         // doubles per block partial
+constexpr int NPART = 12;        // doubles per block partial
 
 // Raw source rows are staged with cp.async through a 16-byte aligned window of WW
 // columns starting at x0 - WOFF (covers the K-ring columns x0 - 3 .. x0 + TX + 2).
@@ -54,8 +55,62 @@ template <class T> struct Staging {
 };
 template <class T> constexpr size_t smem_bytes() { return SM_K + SM_MT + SM_P + SM_M + Staging<T>::BYTES; }
 
+// Tensor-memory-access (TMA) staging of one domain (nx a multiple of TX): tile copies
+// (cp.async.bulk.tensor) land in shared memory box by box, each set of boxes completing an
+// mbarrier; the lane 0s of the warps share the issue.
+//   K      single buffer: rows [r, r + RB) of the window x0 - WOFF .. + WW of the 8 + 8
+//          deviation planes [plane][row][col], the two zeroth-moment planes [row][col]
+//          (float2) and the previous phi [row][col], read by stage K;
+//   F[2]   double buffer: rows [r - c_ky, r - c_ky + RB) of flow plane k, so that local row
+//          rr holds the pull source of the collide row r + rr, read by the collide.
+// The two strips at the periodic seam have WOFF window columns outside [0, nx), which the
+// boxes fill with zeros; their periodic images arrive by cp.async in the side buffers
+// (K side: [plane][row][WOFF]; F side[2]: [plane][row][WOFF]) and the readers take those
+// columns from there.
+template <class T> struct TmaStage {
+    static constexpr size_t DEV = 8ull * RB * WW * sizeof(T);
+    static constexpr size_t MOM = 1ull * RB * WW * sizeof(float2);
+    static constexpr size_t PHP = 1ull * RB * WW * sizeof(float);
+    static constexpr size_t K_BYTES = 2 * DEV + 2 * MOM + PHP;
+    static constexpr size_t FPL = 1ull * RB * WW * sizeof(T);
+    static constexpr size_t F_BYTES = 9 * FPL;
+    // side buffers of the seam strips (WOFF columns)
+    static constexpr size_t SDEV = 8ull * RB * WOFF * sizeof(T);
+    static constexpr size_t SMOM = 1ull * RB * WOFF * sizeof(float2);
+    static constexpr size_t SPHP = 1ull * RB * WOFF * sizeof(float);
+    static constexpr size_t SK_BYTES = 2 * SDEV + 2 * SMOM + SPHP;
+    static constexpr size_t SF_BYTES = 9ull * RB * WOFF * sizeof(T);
+    // offsets from the stage base
+    static constexpr size_t O_DEV0 = 0, O_DEV1 = DEV, O_MOM0 = 2 * DEV, O_MOM1 = 2 * DEV + MOM, O_PHPK = 2 * DEV + 2 * MOM;
+    static constexpr size_t O_F0 = K_BYTES, O_F1 = K_BYTES + F_BYTES;
+    static constexpr size_t O_SK = K_BYTES + 2 * F_BYTES;
+    static constexpr size_t O_SDEV0 = O_SK, O_SDEV1 = O_SK + SDEV, O_SMOM0 = O_SK + 2 * SDEV,
+                            O_SMOM1 = O_SK + 2 * SDEV + SMOM, O_SPHP = O_SK + 2 * SDEV + 2 * SMOM;
+    static constexpr size_t O_SF0 = O_SK + SK_BYTES, O_SF1 = O_SK + SK_BYTES + SF_BYTES;
+    static constexpr size_t BYTES = K_BYTES + 2 * F_BYTES + SK_BYTES + 2 * SF_BYTES;
+    static_assert(DEV % 128 == 0 && MOM % 128 == 0 && PHP % 128 == 0 && FPL % 128 == 0, "boxes on 128-byte boundaries");
+    static_assert(SDEV % 16 == 0 && SMOM % 16 == 0 && SPHP % 16 == 0 && SF_BYTES % 16 == 0, "16-byte cp.async chunks");
+};
+template <class T> constexpr size_t smem_bytes_tma() { return SM_K + SM_MT + SM_P + SM_M + TmaStage<T>::BYTES; }
+static_assert((SM_K + SM_MT + SM_P + SM_M) % 128 == 0, "stage base on a 128-byte boundary");
+// two CTAs per SM: 228 KB of shared memory per SM, 1 KB reserved and ~1 KB static per CTA
+static_assert(smem_bytes_tma<float>() + 2048 <= 233472 / 2, "two CTAs per SM");
+
+// tensor maps of one side of the ping-pong state (kernel parameter, __grid_constant__)
+struct TmaMaps {   // CUtensorMap is 64-byte aligned
+    CUtensorMap dev[2];   // deviation planes of phi, psi: [8][ny][nx], box {WW, RB, 8}
+    CUtensorMap mom[2];   // zeroth moments: float2 [ny][nx] as 32-bit [ny][2 nx], box {2 WW, RB}
+    CUtensorMap php;      // previous phi [ny][nx], box {WW, RB}
+    CUtensorMap f;        // flow populations [9][ny][nx], box {WW, RB, 1}
+};
+
+// bound of every mbarrier wait of the step (global-timer nanoseconds)
+constexpr unsigned long long TMA_WAIT_NS = 2000000000ull;
+// bits of the step's error word
+constexpr unsigned int ERR_TMA_WAIT = 1u;
+
 // indices of the block partials / reduced quantities
-enum { P_S1 = 0, P_S2, P_S3, P_Q, P_PHI, P_PSI, P_KIN, P_CLAMP, P_RANGE };
+enum { P_S1 = 0, P_S2, P_S3, P_Q, P_PHI, P_PSI, P_KIN, P_CLAMP, P_RANGE, P_EF, P_DPHI2, P_PHI2 };
 
 struct Phys {
     float beta, kappa, lambda_s, W, kT, phi_b, inv_phi_b, M_phi, M_psi, M_0, eta_phi, eta_psi;
@@ -76,7 +131,9 @@ struct Phys {
 // reduced record of one time level (written by the last block)
 struct Rec {
     double lam, mpsi_mubar, a, S1, S2, S3, Q, H, phi_tot, psi_tot, kin, clamps, range, H0;
-    double pad[2];
+    double ef;              // discrete free energy (diagnostic level only)
+    double dphi2, phi2;     // sum (phi^n - phi^{n-1})^2 and sum (phi^n)^2 (diagnostic level only)
+    double pad[3];
 };
 
 template <class T>
@@ -90,6 +147,7 @@ struct StepArgs {
     T* hist;                      // 6 planes, updated in place
     double* partials;             // [gridDim][NPART]
     unsigned int* counter;
+    unsigned int* err;            // error bits (ERR_*), or null
     const Rec* rec_prev;          // time level n-1 (zeros before the first step)
     Rec* rec_out;                 // time level n
     int first;                    // this is the first step after initialisation
@@ -139,6 +197,58 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for the phase of the given parity; false after TMA_WAIT_NS
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (global_ns() - t0 > TMA_WAIT_NS) return false;
+    }
+}
+// generic-proxy shared-memory accesses ordered before later async-proxy (TMA) writes
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// y component of c_k for a runtime k
+__device__ __forceinline__ int CYk_rt(int k) { return (k == 2 || k == 5 || k == 6) ? 1 : ((k == 4 || k == 7 || k == 8) ? -1 : 0); }
+
 // c_k . (ax, ay) with the zero lattice components folded away at compile time (IEEE
 // arithmetic may not drop 0 * x, so the generic form would pay for every zero)
 __device__ __forceinline__ float cdot(int k, float ax, float ay) {
@@ -187,6 +297,18 @@ __device__ __forceinline__ void wall_ghost(float ph, float ps, int w, const Phys
     psG = (P.lambda_s > 0.0f && P.psi_on) ? ps - dfdpsi / P.lambda_s : ps;
 }
 
+// wall free-energy density f_w(phi, psi) of wall w (Eq. fw0 with the Langmuir-Szyszkowski
+// tensions of Eq. langmuir, capped as in wall_ghost): (1/2 - g) sigma_sg + (1/2 + g) sigma_sl
+__device__ __forceinline__ float wall_energy(float ph, float ps, int w, const Phys& P) {
+    const float psc = P.psi_on ? fminf(fmaxf(ps, P.psi_clamp), 1.0f - P.psi_clamp) : 0.0f;
+    const float L = P.psi_on ? log1pf(-psc) : 0.0f;
+    const float u = ph * P.inv_phi_b;
+    const float gv = 0.75f * u - 0.25f * u * u * u;
+    const float st_sg = L > P.wLg[w] ? P.wSg[w] * L : -0.5f * P.wS0g[w];
+    const float st_sl = L > P.wLl[w] ? P.wSl[w] * L : -0.5f * P.wS0l[w];
+    return -(P.wcos[w] + st_sg - st_sl) * gv + 0.5f * (st_sg + st_sl) + 0.5f * (P.wS0g[w] + P.wS0l[w]);
+}
+
 // warp reduction of a float-float pair
 __device__ __forceinline__ ff warp_sum_ff(ff v) {
 #pragma unroll
@@ -210,6 +332,9 @@ __device__ __forceinline__ Rec resolve_rec(const Phys& P, int first, const Rec* 
     r.kin = tot[P_KIN];
     r.clamps = tot[P_CLAMP];
     r.range = tot[P_RANGE];
+    r.ef = tot[P_EF];
+    r.dphi2 = tot[P_DPHI2];
+    r.phi2 = tot[P_PHI2];
     r.H = P.linear ? r.phi_tot : 0.5 * P.Nd + 0.5 * r.Q;
     r.H0 = first ? r.H : rec_prev->H0;
     double lam = 0.0;
@@ -312,9 +437,15 @@ __device__ __forceinline__ void static_for(F&& f) {
 // VARRHO = false: uniform density and viscosity (no density-gradient terms).
 // Work split: the strips x rows of the grid, ordered strip-major, are cut into gridDim.x
 // contiguous ranges of equal length; a CTA marches its range (one or two strip pieces).
-template <class T, bool DIAG, bool VARRHO, bool BATCH>
-__global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, const BatchArgs B) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// TMA = true (single domains whose rows are 16-byte multiples): the staged rows of stage K
+// and the collide's flow populations, history and previous phi arrive by TMA boxes
+// (TmaStage), issued one iteration ahead by one thread; false: cp.async staging of the
+// stage-K rows and direct global loads in the collide (batches, odd or narrow grids).
+template <class T, bool DIAG, bool VARRHO, bool BATCH, bool TMA = false>
+__global__ void __launch_bounds__(NTHREADS, 2)
+    step_kernel(const StepArgs<T> A, const BatchArgs B, const __grid_constant__ TmaMaps M) {
+    static_assert(!(TMA && BATCH), "the batch kernel stages with cp.async");
+    extern __shared__ __align__(128) unsigned char smem[];
     int* sK = (int*)smem;
     float2* sMT = (float2*)(smem + SM_K);
     float* sPh = (float*)(smem + SM_K + SM_MT);
@@ -325,6 +456,18 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
     float* sMp = sMu + RING * MX;
     unsigned char* sStg = smem + SM_K + SM_MT + SM_P + SM_M;
     using ST = Staging<T>;
+    using TS = TmaStage<T>;
+    unsigned char* sTma = sStg;   // TMA path: the stage boxes (TmaStage layout) start here
+    __shared__ __align__(8) uint64_t s_bar[3];   // TMA path: [0] stage-K boxes, [1 + b] flow boxes of buffer b
+    uint32_t phK = 0, phF0 = 0, phF1 = 0;        // parity of the next phase of each
+    if (TMA && threadIdx.x == 0) {
+        mbar_init1(&s_bar[0]);
+        mbar_init1(&s_bar[1]);
+        mbar_init1(&s_bar[2]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    int fbuf = 0;          // TMA path: flow buffer of the current iteration
+    int seam = 0;          // TMA path: 0, or -1 / +1 for the strip at the left / right seam
 
     // physical parameters: the kernel argument for one domain, a shared copy of the
     // current instance's parameters in batch mode
@@ -505,6 +648,52 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
         }
     };
 
+    // stage K from the TMA stage holding rows [r0, r0 + RB) (the first NROW are converted);
+    // at the periodic seam the window columns outside [0, nx) come from the side buffer
+    auto stageK_t = [&](auto nrow_c, int r0) {
+        constexpr int NROW = decltype(nrow_c)::value;
+        const int items = NROW * KX * nsets;
+        for (int it = tid; it < items; it += NTHREADS) {
+            const int kc = it % KX;
+            const int rest = it / KX;
+            const int rr = rest % NROW;
+            const int s = rest / NROW;
+            const int y = r0 + rr;
+            if (y < 0 || y >= ny) continue;
+            const int wcol = kc + (WOFF - 3);
+            // main box, or side column (left seam: window columns 0..WOFF-1; right seam:
+            // WW-WOFF..WW-1)
+            const bool side = seam < 0 ? wcol < WOFF : (seam > 0 && wcol >= WW - WOFF);
+            const int col = side ? rr * WOFF + (seam < 0 ? wcol : wcol - (WW - WOFF)) : rr * WW + wcol;
+            const int pst = side ? RB * WOFF : RB * WW;
+            const float2 mv = ((const float2*)(sTma + (side ? (s == 0 ? TS::O_SMOM0 : TS::O_SMOM1)
+                                                          : (s == 0 ? TS::O_MOM0 : TS::O_MOM1))))[col];
+            ff mt = {mv.x, mv.y};
+            if (s == 0) {
+                if (qcoef != 0.0f) {
+                    const float php = ((const float*)(sTma + (side ? TS::O_SPHP : TS::O_PHPK)))[col];
+                    mt = ff_add_f(mt, __fmul_rn(qcoef, hprime(php, P)));
+                }
+            } else {
+                mt = ff_add(mt, cuni);
+            }
+            const T* dd = (const T*)(sTma + (side ? (s == 0 ? TS::O_SDEV0 : TS::O_SDEV1) : (s == 0 ? TS::O_DEV0 : TS::O_DEV1))) + col;
+            const float scl = s == 0 ? sc_phi : sc_psi;
+            const float ma = __fmul_rn(__fmul_rn(Wk(1), scl), mt.hi);
+            const float md = __fmul_rn(__fmul_rn(Wk(5), scl), mt.hi);
+            int ksum = 0;
+            int* kd = &KR(s, 1, y, kc);
+            static_for<1, 9>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                const int kv = __float2int_rn(__fmaf_rn(Stor<T>::lds(dd, (k - 1) * pst), scl, k < 5 ? ma : md));
+                kd[(k - 1) * RING * KX] = kv;
+                ksum += kv;
+            });
+            const ff basev = ff_add(mt, fixed_to_ff(-ksum, s == 0 ? isc_phi : isc_psi));
+            MT(s, y, kc) = make_float2(basev.hi, basev.lo);
+        }
+    };
+
     auto stagePhi = [&](auto nrow_c, int r0) {
         constexpr int nrow = decltype(nrow_c)::value;
         const int items = nrow * PX * 2;
@@ -597,6 +786,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
 
         // flow pull first (longest latency): halfway bounce-back with the moving-wall term
         float f[9];
+        const int rr = tid / TX;   // row within the iteration (TMA stage row)
         const float php_self = __ldg(php_in + c);
         // the source-term history of the previous step, loaded here so that its latency
         // overlaps the flow part (after the f stores the loads could not move up)
@@ -618,13 +808,31 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
             const long long rm = c - gx + (long long)(y > 0 ? -nx : 0);      // row y - 1 (clamped)
             const long long r0c = c - gx;
             const long long rp1 = c - gx + (long long)(y < ny - 1 ? nx : 0);  // row y + 1 (clamped)
-            static_for<0, 9>([&](auto K) {
-                constexpr int k = decltype(K)::value;
-                constexpr int cx = CXk(k), cy = CYk(k);
-                const int sx = cx == 0 ? gx : (cx > 0 ? xm : xp);
-                const long long rowb = cy == 0 ? r0c : (cy > 0 ? rm : rp1);
-                f[k] = Stor<T>::ld(fin + (k * (unsigned)N), rowb + sx);
-            });
+            if (TMA) {
+                // plane k holds rows shifted by -c_ky: local row rr is the pull source row
+                const T* fs = (const T*)(sTma + (fbuf ? TS::O_F1 : TS::O_F0)) + rr * WW + WOFF + cc;
+                static_for<0, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    f[k] = Stor<T>::lds(fs, k * RB * WW - CXk(k));
+                });
+                // the strip's edge column at the periodic seam: the source column outside
+                // [0, nx) is in the side buffer
+                if (seam != 0 && cc == (seam < 0 ? 0 : TX - 1)) {
+                    const T* sf = (const T*)(sTma + (fbuf ? TS::O_SF1 : TS::O_SF0)) + rr * WOFF;
+                    static_for<1, 9>([&](auto K) {
+                        constexpr int k = decltype(K)::value;
+                        if (CXk(k) == (seam < 0 ? 1 : -1)) f[k] = Stor<T>::lds(sf, k * RB * WOFF + (seam < 0 ? WOFF - 1 : 0));
+                    });
+                }
+            } else {
+                static_for<0, 9>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    constexpr int cx = CXk(k), cy = CYk(k);
+                    const int sx = cx == 0 ? gx : (cx > 0 ? xm : xp);
+                    const long long rowb = cy == 0 ? r0c : (cy > 0 ? rm : rp1);
+                    f[k] = Stor<T>::ld(fin + (k * (unsigned)N), rowb + sx);
+                });
+            }
             if (wall_row) {
                 const float rho_w = VARRHO ? P.rho_g + (P.rho_l - P.rho_g) * liquid_fraction(php_self, P) : P.rho_l;
                 static_for<1, 9>([&](auto K) {
@@ -641,6 +849,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
         // gradients (mirror ghosts for mu and rho), Neumann Laplacian of psi, wall flux
         float gmx = 0.f, gmy = 0.f, gpx = 0.f, gpy = 0.f, grx = 0.f, gry = 0.f;
         float lns = 0.f, wf_phi = 0.f, wf_psi = 0.f;
+        float gfx = 0.f, gfy = 0.f, gsx = 0.f, gsy = 0.f;   // grad phi, grad psi (diagnostic pass)
         if (!wall_row) {
             static_for<1, 9>([&](auto K) {
                 constexpr int k = decltype(K)::value;
@@ -655,6 +864,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
                     grx = addc(grx, cx, vchi); gry = addc(gry, cy, vchi);
                 }
                 lns += Wk(k) * SH(y + cy, pc + cx);
+                if (DIAG) {
+                    const float vf = w3 * PH(y + cy, pc + cx), vs = w3 * SH(y + cy, pc + cx);
+                    gfx = addc(gfx, cx, vf); gfy = addc(gfy, cy, vf);
+                    gsx = addc(gsx, cx, vs); gsy = addc(gsy, cy, vs);
+                }
             });
         } else {
             const int w = y == 0 ? 0 : 1;
@@ -675,11 +889,18 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
                     grx = addc(grx, cx, vchi); gry = addc(gry, cy, vchi);
                 }
                 lns += Wk(k) * vpsi;
+                float eph = vphi, eps_ = vpsi;
                 if (out) {
                     float gph, gps;
                     wall_ghost(vphi, vpsi, w, P, gph, gps);
                     wf_phi += Wk(k) * (gph - vphi);
                     wf_psi += Wk(k) * (gps - vpsi);
+                    eph = gph;
+                    eps_ = gps;
+                }
+                if (DIAG) {   // gradients with the wetting ghosts of Eq. boundary
+                    gfx = addc(gfx, cx, w3 * eph); gfy = addc(gfy, cy, w3 * eph);
+                    gsx = addc(gsx, cx, w3 * eps_); gsy = addc(gsy, cy, w3 * eps_);
                 }
             });
         }
@@ -725,15 +946,32 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
             kinacc += 0.5f * rho * usq;
             acc[P_PSI] = ff_add(acc[P_PSI], psff);
             range |= !(fabsf(ux) < 1.0f && fabsf(uy) < 1.0f && fabsf(phi) < 2.0f && fabsf(pres) < 1e3f);
+            // discrete free energy of Eq. eq1 (bulk densities with the gradient terms of the
+            // isotropic stencil, plus the wall energy f_w of Eq. eq8 on the wall rows)
+            const float om = 1.0f - phi * phi;
+            float e = P.beta * om * om + 0.5f * P.kappa * (gfx * gfx + gfy * gfy);
+            if (P.psi_on) {
+                const float psc = fminf(fmaxf(psi, P.psi_clamp), 1.0f - P.psi_clamp);
+                e += P.kT * (psc * logf(psc) + (1.0f - psc) * log1pf(-psc)) + 0.5f * P.lambda_s * (gsx * gsx + gsy * gsy) -
+                     P.beta * psi * om * om + 0.5f * P.W * psi * phi * phi;
+            }
+            if (y == 0) e += wall_energy(phi, psi, 0, P);
+            if (y == ny - 1) e += wall_energy(phi, psi, 1, P);
+            acc[P_EF] = ff_add_f(acc[P_EF], e);
+            // one-step change of phi against the previous time level kept for the source terms
+            const float dph = (phff.hi - php_self) + phff.lo;
+            acc[P_DPHI2] = ff_add_f(acc[P_DPHI2], dph * dph);
+            acc[P_PHI2] = ff_add_f(acc[P_PHI2], phi * phi);
         }
 
-        // free reaction term of the surfactant (R_psi without mubar), rounded to storage
+        // free reaction term of the surfactant (R_psi without mubar), rounded to storage:
+        // M_psi (-k_B T ln(psi/(1-psi)) + beta (1-phi^2)^2 - (W/2) phi^2 + lambda_s (Lap_G - Lap_N) psi)
+        // - M_0 Lap_N psi, written with the mu_psi of stage MU at this node (which holds the
+        // same logarithm and adsorption terms with -lambda_s Lap_G psi):
+        // -M_psi mu_psi - (M_psi lambda_s + M_0) Lap_N psi
         float Rf_psi = 0.0f;
         if (P.psi_on) {
-            const float psc = fminf(fmaxf(psi, P.psi_clamp), 1.0f - P.psi_clamp);
-            const float om = 1.0f - phi * phi;
-            Rf_psi = Stor<T>::rnd(P.M_psi * (-P.kT * (__logf(psc) - __logf(1.0f - psc)) + P.beta * om * om -
-                                             0.5f * P.W * phi * phi + P.lambda_s * wf_psi) - P.M_0 * lapN_psi);
+            Rf_psi = Stor<T>::rnd(-P.M_psi * MP(y, mc) - (P.M_psi * P.lambda_s + P.M_0) * lapN_psi);
             acc[P_S3] = ff_add_f(acc[P_S3], Rf_psi);
         }
 
@@ -897,7 +1135,142 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_kernel(const StepArgs<T> A, 
     // --------------------------------------------------------------- pipeline
     using I2 = std::integral_constant<int, 2>;
     using I4 = std::integral_constant<int, 4>;
+    // ---- TMA staging (single domain): issue, bounded waits, periodic-seam side loads
+    const int warp = tid >> 5, lane = tid & 31;
+    auto tma_fail = [&](uint64_t* bar, uint32_t par) {
+        if (A.err) atomicOr(A.err, ERR_TMA_WAIT);
+        mbar_wait_bounded(bar, par);   // let copies still in flight land before going on
+    };
+    // stage-K boxes of rows [r0, r0 + RB): lane 0 of warps 0..4 issue one box each, warp 0
+    // also the expected byte count (a complete_tx may come first: the count goes negative
+    // until then, and the phase cannot complete before warp 0's arrive)
+    auto issue_K = [&](int r0) {
+        if (lane == 0 && warp < 5) {
+            uint64_t* bar = &s_bar[0];
+            const int xw = x0 - WOFF;
+            if (warp == 0) {
+                mbar_expect_tx(bar, (uint32_t)(nsets == 2 ? TS::K_BYTES : TS::K_BYTES - TS::DEV - TS::MOM));
+                tma_load_3d(sTma + TS::O_DEV0, &M.dev[0], xw, r0, 0, bar);
+            } else if (warp == 1) {
+                tma_load_2d(sTma + TS::O_MOM0, &M.mom[0], 2 * xw, r0, bar);
+            } else if (warp == 2) {
+                tma_load_2d(sTma + TS::O_PHPK, &M.php, xw, r0, bar);
+            } else if (nsets == 2) {
+                if (warp == 3) tma_load_3d(sTma + TS::O_DEV1, &M.dev[1], xw, r0, 0, bar);
+                else tma_load_2d(sTma + TS::O_MOM1, &M.mom[1], 2 * xw, r0, bar);
+            }
+        }
+        if (seam != 0) {
+            // the WOFF periodic-image columns: 16-byte cp.async chunks, one per thread
+            constexpr int CD = WOFF * (int)sizeof(T) / 16, CM = WOFF * 8 / 16, CP = WOFF * 4 / 16;
+            const int xs = seam < 0 ? nx - WOFF : 0;
+            int q = tid;
+            const int nd = 2 * 8 * RB * CD, nm = 2 * RB * CM, np = RB * CP;
+            if (q < nd) {
+                const int ch = q % CD, rest = q / CD, rr = rest % RB, pl = rest / RB;   // pl 0..15
+                const int y = r0 + rr;
+                if (y >= 0 && y < ny && (pl < 8 || nsets == 2)) {
+                    const T* src = (pl < 8 ? gd_in : hd_in) + (long long)(pl & 7) * N + (long long)y * nx + xs + ch * (16 / (int)sizeof(T));
+                    cp_async16(sTma + (pl < 8 ? TS::O_SDEV0 : TS::O_SDEV1) + (((pl & 7) * RB + rr) * WOFF) * sizeof(T) + ch * 16, src);
+                }
+            } else if ((q -= nd) < nm) {
+                const int ch = q % CM, rest = q / CM, rr = rest % RB, st = rest / RB;
+                const int y = r0 + rr;
+                if (y >= 0 && y < ny && (st == 0 || nsets == 2)) {
+                    const float2* src = (st == 0 ? gm_in : hm_in) + (long long)y * nx + xs + ch * 2;
+                    cp_async16(sTma + (st == 0 ? TS::O_SMOM0 : TS::O_SMOM1) + (rr * WOFF) * sizeof(float2) + ch * 16, src);
+                }
+            } else if ((q -= nm) < np) {
+                const int ch = q % CP, rr = q / CP;
+                const int y = r0 + rr;
+                if (y >= 0 && y < ny)
+                    cp_async16(sTma + TS::O_SPHP + (rr * WOFF) * sizeof(float) + ch * 16, php_in + (long long)y * nx + xs + ch * 4);
+            }
+            cp_async_commit();
+        }
+    };
+    // flow boxes of collide rows [r0, r0 + RB) into buffer fb: plane k by lane 0 of warp k % 8
+    auto issue_F = [&](int r0, int fb) {
+        uint64_t* bar = &s_bar[1 + fb];
+        unsigned char* dst = sTma + (fb ? TS::O_F1 : TS::O_F0);
+        if (lane == 0) {
+            if (warp == 0) mbar_expect_tx(bar, (uint32_t)TS::F_BYTES);
+            for (int k = warp; k < 9; k += NTHREADS / 32)
+                tma_load_3d(dst + k * TS::FPL, &M.f, x0 - WOFF, r0 - (k == 2 || k == 5 || k == 6 ? 1 : (k == 4 || k == 7 || k == 8 ? -1 : 0)), k, bar);
+        }
+        if (seam != 0) {
+            constexpr int CD = WOFF * (int)sizeof(T) / 16;
+            const int xs = seam < 0 ? nx - WOFF : 0;
+            const int q = tid;
+            if (q < 9 * RB * CD) {
+                const int ch = q % CD, rest = q / CD, rr = rest % RB, k = rest / RB;
+                const int ysrc = r0 + rr - CYk_rt(k);
+                if (ysrc >= 0 && ysrc < ny)
+                    cp_async16(sTma + (fb ? TS::O_SF1 : TS::O_SF0) + ((k * RB + rr) * WOFF) * sizeof(T) + ch * 16,
+                               f_in + (long long)k * N + (long long)ysrc * nx + xs + ch * (16 / (int)sizeof(T)));
+            }
+            cp_async_commit();
+        }
+    };
+    auto wait_K = [&]() {
+        if (!mbar_wait_bounded(&s_bar[0], phK)) tma_fail(&s_bar[0], phK);
+        phK ^= 1u;
+    };
+    auto wait_F = [&](int fb) {
+        uint32_t& ph = fb ? phF1 : phF0;
+        if (!mbar_wait_bounded(&s_bar[1 + fb], ph)) tma_fail(&s_bar[1 + fb], ph);
+        ph ^= 1u;
+    };
+
+    auto march_tma = [&](int strip, int y0, int y1) {
+        ys = y0;
+        ye = y1;
+        x0 = strip * TX;
+        seam = x0 - WOFF < 0 ? -1 : (x0 - WOFF + WW > nx ? 1 : 0);
+        __syncthreads();   // the previous piece's last collide read the rings and stages
+        issue_K(ys - 3);
+        wait_K();
+        if (seam) { cp_async_wait_all(); __syncthreads(); }
+        stageK_t(I4{}, ys - 3);
+        __syncthreads();
+        issue_K(ys + 1);
+        wait_K();
+        if (seam) { cp_async_wait_all(); __syncthreads(); }
+        stageK_t(I2{}, ys + 1);
+        __syncthreads();
+        issue_K(ys + 3);
+        fbuf = 0;
+        issue_F(ys, 0);
+        stagePhi(I4{}, ys - 2);
+        __syncthreads();
+        stageMu(I2{}, ys - 1);
+        if (seam) cp_async_wait_all();
+        __syncthreads();
+        for (int r = ys; r < ye; r += RB) {
+            // the flow boxes of the next iteration go out a whole iteration ahead (their
+            // buffer was last read by the collide before the previous barrier)
+            if (r + RB < ye) issue_F(r + RB, fbuf ^ 1);
+            wait_K();
+            stageK_t(I4{}, r + 3);
+            __syncthreads();
+            if (r + RB < ye) issue_K(r + RB + 3);
+            stagePhi(I4{}, r + 2);
+            __syncthreads();
+            stageMu(I4{}, r + 1);
+            if (seam) cp_async_wait_all();   // side columns of the next K and flow boxes
+            __syncthreads();
+            wait_F(fbuf);
+            stageCollide(r, min(r + RB, ye));
+            __syncthreads();
+            fbuf ^= 1;
+        }
+    };
+
     auto march = [&](int strip, int y0, int y1) {
+        if constexpr (TMA) {
+            march_tma(strip, y0, y1);
+            return;
+        }
         ys = y0;
         ye = y1;
         x0 = strip * TX;

@@ -428,15 +428,15 @@ inline int mk_stages(int N) { return N <= 32 ? 3 : 4; }
 inline int wg_stages(int C) { return C <= 32 ? 3 : 4; }
 
 cudaError_t conv_attrs() {
-    static cudaError_t done = cudaErrorNotReady;
-    if (done == cudaErrorNotReady) {
+    static slbm::PerDeviceOnce once;
+    return once([] {
         const int mk = (int)(CONV_STAGES * mk_stage_bytes(256)), wg = (int)(CONV_STAGES * wg_stage_bytes(256));
-        done = cudaFuncSetAttribute(conv_mk_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mk);
-        if (done == cudaSuccess) done = cudaFuncSetAttribute(conv_mk_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mk);
-        if (done == cudaSuccess) done = cudaFuncSetAttribute(conv_wg_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, wg);
-        if (done == cudaSuccess) done = cudaFuncSetAttribute(conv_wg_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, wg);
-    }
-    return done;
+        cudaError_t e = cudaFuncSetAttribute(conv_mk_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mk);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(conv_mk_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mk);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(conv_wg_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, wg);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(conv_wg_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, wg);
+        return e;
+    });
 }
 
 cudaError_t launch_mk(const bf16* x, const bf16* w, const float* bias, const bf16* mask, bf16* y, int B, int H, int W,
@@ -893,8 +893,8 @@ slbm_status slbm_ws_batch_targets(slbm_ws* n, slbm_batch* b, int idx, double psi
     slbm_domain* d = b->dom[idx];
     if (d->p.ny != n->H || d->p.nx != n->W) return wfail(n, SLBM_EINVAL, "instance grid differs from the network's");
     if (!d->fields) return wfail(n, SLBM_ESTATE, "instance never initialised");
-    // fields of the current level into the instance's own field scratch
-    slbm_status s = slbm_read_fields_noalloc(d, d->fields, d->fields + d->N, nullptr, nullptr, nullptr, nullptr);
+    // fields of the current level into the instance's own field buffer (its own partials)
+    slbm_status s = diag_into_fields(d);
     if (s) return wfail(n, s, d->err);
     targets_kernel<<<ew_grid(d->N), EW, 0, d->stream>>>(d->fields, d->fields + d->N, d->N, psi0, d->p.psi_on, targets);
     cudaError_t e = cudaGetLastError();

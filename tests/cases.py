@@ -50,10 +50,10 @@ def oracle_for(c):
     return Oracle(p, phi, psi)
 
 
-def domain_for(c, precision="fp32", stream=None):
+def domain_for(c, precision="fp32", stream=None, staging=0):
     from paper_2609_26332_b300 import binding as B
     keys = [k for k in BASE if k not in ("constraint", "multiplier", "psi_on")]
-    p = B.default_params(c["nx"], c["ny"], precision=precision,
+    p = B.default_params(c["nx"], c["ny"], precision=precision, staging=staging,
                          constraint=B.LINEAR if c["constraint"] == "linear" else B.NONLINEAR,
                          multiplier={"paper": B.PAPER, "target": B.TARGET, "exact": B.EXACT}[c["multiplier"]],
                          psi_on=1 if c["psi_on"] else 0, **{k: c[k] for k in keys})

@@ -1,7 +1,9 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by
-element, on seeded inputs.  Tolerances: 1e-5 max-abs on phi and psi and 1e-5
-relative (to max |u| of the oracle) on u after the stated steps; conserved totals to
-1e-12 relative."""
+element, on seeded inputs.  Tolerances: 1e-5 max-abs on phi and psi; on u and p 1e-5
+relative to the oracle's max |u|, max |p|, plus an FP32 floor of 2e-8 absolute (u and p
+are moments of FP32 populations of size up to ~1e-2, whose rounding, ~1e-9 per value and
+step, leaves ~1e-8 after a few hundred steps; measured 5e-9 .. 1e-8 on every case);
+conserved totals to 1e-12 relative."""
 import numpy as np
 import pytest
 
@@ -28,14 +30,23 @@ def _compare(c, steps=None, tol_phi=1e-5, tol_u=1e-5, precision="fp32"):
         d.step(steps)
         fg = d.read_fields()
         tg = d.read_totals()
+    umax = max(np.abs(fo["ux"]).max(), np.abs(fo["uy"]).max(), 1e-30)
+    pmax = max(np.abs(fo["p"]).max(), 1e-30)
+    du = max(np.abs(fg["ux"] - fo["ux"]).max(), np.abs(fg["uy"] - fo["uy"]).max())
+    dp = np.abs(fg["p"] - fo["p"]).max()
     err = {
         "phi": np.abs(fg["phi"] - fo["phi"]).max(),
         "psi": np.abs(fg["psi"] - fo["psi"]).max(),
-        "u": max(np.abs(fg["ux"] - fo["ux"]).max(), np.abs(fg["uy"] - fo["uy"]).max())
-        / max(np.abs(fo["ux"]).max(), np.abs(fo["uy"]).max(), 1e-30),
-        "p": np.abs(fg["p"] - fo["p"]).max() / max(np.abs(fo["p"]).max(), 1e-30),
+        "u": du / umax,
+        "p": dp / pmax,
+        # within the stated bound: 1e-5 relative plus the FP32 floor
+        "u_ok": du <= 1e-5 * umax + U_FLOOR,
+        "p_ok": dp <= 1e-5 * pmax + U_FLOOR,
     }
     return err, fo, fg, to, tg
+
+
+U_FLOOR = 2e-8
 
 
 def test_config1_1000_steps():
@@ -43,7 +54,8 @@ def test_config1_1000_steps():
     print("config1 errors", err)
     assert err["phi"] < 1e-5
     assert err["psi"] < 1e-5
-    assert err["u"] < 1e-5
+    assert err["u"] < 1e-5            # max |u| is 1.3e-3 here: well above the floor
+    assert err["p_ok"]
     assert abs(tg["psi_total"] - to["psi_total"]) / to["psi_total"] < 1e-12
     assert tg["clamp_count"] == 0 and tg["range_count"] == 0
     assert abs(tg["lambda_phi"] - to["lam"]) < 1e-4 * abs(to["lam"])
@@ -72,7 +84,7 @@ def test_parity_cases(c):
     print(c["name"], err)
     assert err["phi"] < 1e-5
     assert err["psi"] < 1e-5
-    assert err["u"] < 1e-4
+    assert err["u_ok"] and err["p_ok"]
     if c["psi_on"]:
         assert abs(tg["psi_total"] - to["psi_total"]) / to["psi_total"] < 1e-12
 
@@ -84,7 +96,7 @@ def test_first_step_and_zero_steps():
     # the first pull is exact up to the 2^-30 fixed-point grid of the exchanged populations
     assert err0["phi"] < 1e-7 and err0["psi"] < 1e-7
     err1, *_ = _compare(c, steps=1)
-    assert err1["phi"] < 1e-6 and err1["psi"] < 1e-6 and err1["u"] < 1e-5
+    assert err1["phi"] < 1e-6 and err1["psi"] < 1e-6 and err1["u_ok"] and err1["p_ok"]
 
 
 def test_surfactant_conservation_gpu():
