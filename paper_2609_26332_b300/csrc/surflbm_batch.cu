@@ -261,13 +261,22 @@ slbm_status residuals(slbm_batch* b, long long K, std::vector<double>& r) {
         }
     }
     if (args.empty()) return SLBM_OK;
-    // one scratch allocation per call (residual checks run every K steps)
+    // scratch kept by the batch: sized on the first call (every instance active, the most
+    // it can need: instances only retire), reused by every later check
     const size_t nb = blk_inst.size();
-    char* buf = nullptr;
     const size_t bytes = args.size() * sizeof(ResidualArgs) + nb * (sizeof(int) + sizeof(long long)) +
                          args.size() * 4 * sizeof(double) + 64;
-    cudaError_t e = cudaMalloc(&buf, bytes);
-    if (e != cudaSuccess) return bcuda(b, e, "residual scratch");
+    cudaError_t e = cudaSuccess;
+    if (bytes > b->res_bytes) {
+        cudaFree(b->d_res);
+        b->d_res = nullptr;
+        b->res_bytes = 0;
+        e = cudaMalloc(&b->d_res, bytes);
+        if (e != cudaSuccess) return bcuda(b, e, "residual scratch");
+        b->res_bytes = bytes;
+        b->bytes += bytes;
+    }
+    char* buf = b->d_res;
     double* d_out = (double*)buf;
     ResidualArgs* d_args = (ResidualArgs*)(buf + args.size() * 4 * sizeof(double));
     long long* d_bs = (long long*)((char*)d_args + args.size() * sizeof(ResidualArgs));
@@ -284,7 +293,6 @@ slbm_status residuals(slbm_batch* b, long long K, std::vector<double>& r) {
     std::vector<double> h(args.size() * 4);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    cudaFree(buf);
     if (e != cudaSuccess) return bcuda(b, e, "residual");
     if (b->have_snap) {
         for (size_t k = 0; k < args.size(); ++k) {
@@ -594,6 +602,7 @@ void slbm_batch_destroy(slbm_batch* b) {
     cudaFree(b->d_pieces);
     cudaFree(b->d_partials);
     cudaFree(b->d_counters);
+    cudaFree(b->d_res);
     cudaFree(b->d_queue);
     cudaFree(b->d_G);
     cudaFree(b->d_snap_base);

@@ -79,6 +79,8 @@ struct slbm_batch {
     float* d_snap_base = nullptr;
     std::vector<size_t> snap_off;
     bool have_snap = false;
+    char* d_res = nullptr;            // residual-check scratch (kept between checks)
+    size_t res_bytes = 0;
     std::string err = "no error";
     size_t bytes = 0;
 };
