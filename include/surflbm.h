@@ -301,6 +301,23 @@ size_t slbm_batch_device_bytes(const slbm_batch* b);
 const char* slbm_batch_last_error(const slbm_batch* b);
 void slbm_batch_destroy(slbm_batch* b);
 
+/* Verification hook: the manufactured-solution accuracy test of Sec. 4.1 on the channel.
+ * With m != NULL the domain's steps solve the phi and psi equations driven by the sources
+ * that make
+ *     phi^e = A e^{-t} sin 2pi(x - u t) cos 2pi y,  psi^e = 1/2 + 0.05 e^{-2t} cos 2pi(x - u t) cos 2pi y
+ * exact (physical x, y in [0, 1], node (i, j) at x = i dx, y = (j + 1/2) dx, t = n dt), with
+ * mobility M, beta, kappa, k_B T, W (physical units) and the linear multipliers of that
+ * test; no force acts on the flow, and the next slbm_init_fields starts the flow at the
+ * uniform lattice velocity u dt / dx (set both walls to slide at it).  The caller chooses
+ * the lattice parameters so that the lattice equations are those of the test (sigma, eps
+ * from beta and kappa / dx^2, Ex = 4 beta / W, Pi = k_B T / (4 beta), tau_g = tau_h = 1,
+ * eta_phi = eta_psi = 6 M kappa dt / dx^2, M_psi = M dt, lambda_s = 0, linear constraint).
+ * FP32 storage and uniform density only (EINVAL otherwise); m == NULL switches it off. */
+typedef struct {
+    double amplitude, u, M, beta, kappa, kT, W, dx, dt;
+} slbm_mms;
+slbm_status slbm_set_mms(slbm_domain* d, const slbm_mms* m);
+
 /* Checkpoint / resume.  slbm_save writes the complete state at the current time level
  * (parameters, walls, step count, populations, zeroth moments, previous phi, source-term
  * history and the multiplier records of the last two levels) to a binary file; the

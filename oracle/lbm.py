@@ -85,9 +85,15 @@ class Oracle:
     """Plain FP64 implementation of the paper's coupled LBM (Sec. 3) on a channel:
     x periodic, halfway bounce-back walls below row 0 and above row ny-1."""
 
-    def __init__(self, params, phi0, psi0=None):
+    def __init__(self, params, phi0, psi0=None, u0=(0.0, 0.0), source=None, force=True):
+        """u0: uniform initial velocity (the equilibria of the initial state carry it);
+        source: optional callable n -> (S_phi, S_psi), arrays added to R_phi, R_psi of step
+        n (a manufactured source, lattice units per step); force=False: no force acts on
+        the flow (with walls sliding at u0 the flow stays uniform, a prescribed velocity)."""
         p = params
         self.p = p
+        self.source = source
+        self.force = force
         self.d = derive(p)
         self.ny, self.nx = p.ny, p.nx
         if p.ny < 2 or p.nx < 1:
@@ -100,12 +106,15 @@ class Oracle:
         psi0 = np.asarray(psi0, dtype=np.float64)
         self.Mm = moment_matrix()
         self.Minv = np.linalg.inv(self.Mm)
-        zero = np.zeros_like(phi0)
-        # pre-collision populations at t = 0: equilibria of the initial fields at rest
-        # (f^eq with p = 0, u = 0 vanishes identically)
-        self.f = np.zeros((Q, p.ny, p.nx))
-        self.g = self._scalar_eq(phi0, zero, zero, p.eta_phi)
-        self.h = self._scalar_eq(psi0, zero, zero, p.eta_psi)
+        # pre-collision populations at t = 0: equilibria of the initial fields with p = 0
+        # and the uniform velocity u0 (f^eq vanishes identically at rest)
+        ux0 = np.full_like(phi0, float(u0[0]))
+        uy0 = np.full_like(phi0, float(u0[1]))
+        rho0 = p.rho_g + (p.rho_l - p.rho_g) * np.clip(0.5 * (phi0 / self.d.phi_b + 1.0), 0.0, 1.0)
+        cu0 = _CXf * ux0 + _CYf * uy0
+        self.f = rho0 * _Wf * (cu0 / CS2 + cu0 * cu0 / (2 * CS2 ** 2) - (ux0 * ux0 + uy0 * uy0) / (2 * CS2))
+        self.g = self._scalar_eq(phi0, ux0, uy0, p.eta_phi)
+        self.h = self._scalar_eq(psi0, ux0, uy0, p.eta_psi)
         self.first = True
         self.n = 0
         self.R_prev_phi = None
@@ -310,8 +319,12 @@ class Oracle:
         mpP = _pad(mu_psi, mu_psi[0], mu_psi[-1])
         gmx, gmy = gradient(muP, ny, nx)
         gpx, gpy = gradient(mpP, ny, nx)
-        Fx = -phi * gmx - psi * gpx + p.Gx
-        Fy = -phi * gmy - psi * gpy + p.Gy
+        if self.force:
+            Fx = -phi * gmx - psi * gpx + p.Gx
+            Fy = -phi * gmy - psi * gpy + p.Gy
+        else:
+            Fx = np.zeros((ny, nx))
+            Fy = np.zeros((ny, nx))
         # liquid fraction, clipped to [0, 1]: the bulk |phi| exceeds phi_b(psi_b) wherever
         # the bulk surfactant falls below psi_b (Sec. 2.2), and rho, nu stay within the
         # pure-phase values (at rho_l / rho_g = 1000 an unclipped chi of -1e-3 gives rho ~ 0)
@@ -367,6 +380,11 @@ class Oracle:
                      + d.M_psi * d.lambda_s * (e["LG_psi"] - e["LN_psi"]) - d.M_0 * e["LN_psi"])
         else:
             R_psi = np.zeros((ny, nx))
+        if self.source is not None:
+            S_phi, S_psi = self.source(self.n)
+            R_phi = R_phi + S_phi
+            if p.psi_on:
+                R_psi = R_psi + S_psi
         phiu = np.stack([phi * ux, phi * uy])
         psiu = np.stack([psi * ux, psi * uy])
         if self.first:   # first step: the backward differences start from zero

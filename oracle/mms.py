@@ -137,3 +137,79 @@ def run(n, t_end=5.0, dt_factor=0.15):
     e_phi = math.sqrt(float(np.sum((phi - pe) ** 2) / np.sum(pe ** 2)))
     e_psi = math.sqrt(float(np.sum((psi - qe) ** 2) / np.sum(qe ** 2)))
     return e_phi, e_psi, steps, abs(phi.sum() - sum0[0]) / sum0[1], abs(psi.sum() - sum0[2]) / sum0[2]
+
+
+# ------------------------------------------------------------------ channel variant
+# The same test on the channel geometry of the full step (x periodic, halfway walls at
+# y = 0 and y = 1): the walls admit no normal velocity and a 90-degree neutral wall fixes
+# zero normal gradients, so the prescribed velocity is (0.05, 0) and both manufactured
+# fields vary as cos(2 pi y) across the channel:
+#
+#     phi^e = a e^{-t} sin 2pi(x - u_x t) cos 2pi y
+#     psi^e = 0.5 + 0.05 e^{-2t} cos 2pi(x - u_x t) cos 2pi y
+#
+# The means of the potentials keep the closed forms above (sin^2, cos^2 average 1/2 and
+# sin^4, cos^4 3/8 on the node sets used here; the logarithm is odd in cos X).  The run
+# goes through the full Oracle (flow populations at the uniform velocity, walls sliding
+# with it, no force on the flow, the nonlinear-free linear constraint), with the
+# lattice parameters below.
+
+U_CH = (0.05, 0.0)
+
+
+def channel_exact(x, y, t):
+    X = 2.0 * math.pi * (x - U_CH[0] * t)
+    Y = 2.0 * math.pi * y
+    a = AMP * math.exp(-t)
+    return a * np.sin(X) * np.cos(Y), 0.5 + 0.05 * math.exp(-2.0 * t) * np.cos(X) * np.cos(Y)
+
+
+def channel_sources(x, y, t):
+    pe, qe = channel_exact(x, y, t)
+    lap_pe = -8.0 * math.pi ** 2 * pe
+    s_phi = -pe + M * (mu_phi_bulk(pe, qe) - KAPPA * lap_pe)
+    s_psi = -2.0 * (qe - 0.5) + M * (mu_psi_bulk(pe, qe) - mubar_psi_exact(t))
+    return s_phi, s_psi
+
+
+def channel_setup(n, dt_factor=0.15):
+    """OracleParams, node coordinates, dx, dt and the lattice velocity of the channel test
+    on n x n nodes (node (i, j) at x = i dx, y = (j + 1/2) dx)."""
+    from .params import OracleParams, Wall
+    dx = 1.0 / n
+    dt = dx * dx / dt_factor
+    kappa_l = KAPPA / (dx * dx)                  # -kappa lap = -(kappa / dx^2) lap_lattice
+    m_l = M * dt                                 # mobility per step
+    D = m_l * kappa_l                            # lattice diffusion, = eta c_s^2 (tau - 1/2) at tau = 1
+    u_l = U_CH[0] * dt / dx
+    # sigma, eps from beta = 3 sigma / (4 eps), kappa = 3 eps sigma / 8; W = 4 beta / Ex;
+    # k_B T = 4 beta Pi; M_phi kappa = eta c_s^2 (tau - 1/2) gives eta = 6 D; psi gets the same
+    # lattice diffusion and M_0 = D cancels it (lambda_s = 0)
+    p = OracleParams(nx=n, ny=n, tau_f=1.0, tau_g=1.0, tau_h=1.0,
+                     sigma=math.sqrt(32.0 * BETA * kappa_l / 9.0), eps=math.sqrt(2.0 * kappa_l / BETA),
+                     Ex=4.0 * BETA / WADS, Pi=KT / (4.0 * BETA), M_psi=m_l, eta_phi=6.0 * D, eta_psi=6.0 * D,
+                     lambda_s=0.0, phi_b=1.0, constraint="linear", multiplier="paper",
+                     walls=[Wall(90.0, 0.0, 0.0, u_l), Wall(90.0, 0.0, 0.0, u_l)])
+    c = np.arange(n) * dx
+    x, y = np.meshgrid(c, c + 0.5 * dx)
+    return p, x, y, dx, dt, u_l
+
+
+def run_channel(n, t_end=5.0):
+    """(E2_phi, E2_psi, steps, drift_psi) of the channel test through the full Oracle."""
+    p, x, y, dx, dt, u_l = channel_setup(n)
+    steps = int(round(t_end / dt))
+    phi0, psi0 = channel_exact(x, y, 0.0)
+
+    def source(k):
+        s_phi, s_psi = channel_sources(x, y, k * dt)
+        return dt * s_phi, dt * s_psi
+
+    o = Oracle(p, phi0, psi0, u0=(u_l, 0.0), source=source, force=False)
+    sum0 = psi0.sum()
+    o.step(steps)
+    f = o.fields()
+    pe, qe = channel_exact(x, y, steps * dt)
+    e_phi = math.sqrt(float(np.sum((f["phi"] - pe) ** 2) / np.sum(pe ** 2)))
+    e_psi = math.sqrt(float(np.sum((f["psi"] - qe) ** 2) / np.sum(qe ** 2)))
+    return e_phi, e_psi, steps, abs(f["psi"].sum() - sum0) / sum0, f

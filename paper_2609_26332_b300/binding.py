@@ -47,6 +47,10 @@ class WallSpec(ctypes.Structure):
                 ("u_x", ctypes.c_double)]
 
 
+class MMS(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("amplitude", "u", "M", "beta", "kappa", "kT", "W", "dx", "dt")]
+
+
 class Totals(ctypes.Structure):
     _fields_ = [
         ("step", ctypes.c_longlong), ("Q_phi", ctypes.c_double), ("H", ctypes.c_double),
@@ -78,6 +82,7 @@ def _load():
     L.slbm_workspace_bytes.argtypes = [ctypes.POINTER(Params)]
     L.slbm_workspace_bytes.restype = ctypes.c_size_t
     L.slbm_create_domain_ext.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+    L.slbm_set_mms.argtypes = [vp, ctypes.POINTER(MMS)]
     L.slbm_save.argtypes = [vp, ctypes.c_char_p]
     L.slbm_load.argtypes = [vp, ctypes.c_char_p]
     L.slbm_destroy.argtypes = [vp]
@@ -86,7 +91,8 @@ def _load():
     L.slbm_last_error.restype = ctypes.c_char_p
     L.slbm_version.restype = ctypes.c_char_p
     for name in ("slbm_create_domain", "slbm_set_walls", "slbm_init_fields", "slbm_step",
-                 "slbm_read_fields", "slbm_read_totals", "slbm_create_domain_ext", "slbm_save", "slbm_load"):
+                 "slbm_read_fields", "slbm_read_totals", "slbm_create_domain_ext", "slbm_save", "slbm_load",
+                 "slbm_set_mms"):
         getattr(L, name).restype = ctypes.c_int
     # batches
     L.slbm_create_batch.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(WallSpec), i, vp, ctypes.POINTER(vp)]
@@ -205,6 +211,14 @@ class Domain:
             raise SlbmError(st, lib.slbm_last_error(None).decode())
         self.params = params
         self._workspace = workspace
+
+    def set_mms(self, **kw):
+        """slbm_set_mms with the test's physical parameters (None switches it off)."""
+        if not kw:
+            self._check(lib.slbm_set_mms(self._h, None))
+            return
+        m = MMS(**kw)
+        self._check(lib.slbm_set_mms(self._h, ctypes.byref(m)))
 
     def save(self, path):
         self._check(lib.slbm_save(self._h, os.fsencode(path)))

@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 
 using namespace slbm;
 
@@ -26,6 +27,7 @@ struct InitArgs {
     const double* psi0;
     double eta_phi, eta_psi, rho_l, rho_g, inv_phi_b;
     double uw[2];
+    double u0x;          // uniform initial velocity (x), 0 except in the manufactured-solution test
     int psi_on;
 };
 
@@ -54,7 +56,9 @@ __global__ void init_kernel(InitArgs a, T* f, T* gd, float2* gm, T* hd, float2* 
             if (ty < 0 || ty >= a.ny) ty = y;
             tx = wrapx(tx, a.nx);
             const double ft = (set == 1 && !a.psi_on) ? 0.0 : F[(long long)ty * a.nx + tx];
-            gk[k] = WkD(k) * eta * ft;
+            // w_k (eta c + c_k . (c u) / c_s^2) at the target; u = (u0x, 0) keeps it the same
+            // for the specular partner of a wall link
+            gk[k] = WkD(k) * (eta + 3.0 * CXk(k) * a.u0x) * ft;
             msum += gk[k];
         }
         float2 mv;
@@ -63,11 +67,25 @@ __global__ void init_kernel(InitArgs a, T* f, T* gd, float2* gm, T* hd, float2* 
         m[c] = mv;
         for (int k = 1; k < 9; ++k) Stor<T>::st(d, (long long)(k - 1) * a.N + c, (float)(gk[k] - (double)Wk(k) * mv.x));
     }
-    const double rho = a.rho_g + (a.rho_l - a.rho_g) * 0.5 * (a.phi0[c] * a.inv_phi_b + 1.0);
+    // flow: the equilibrium f^eq_k(rho, u0) (p = 0) of the node the population streams to;
+    // a link into a wall stores what the moving-wall bounce-back turns into f^eq of the
+    // opposite direction at this node
+    auto rho_at = [&](long long i) {
+        return a.rho_g + (a.rho_l - a.rho_g) * fmin(fmax(0.5 * (a.phi0[i] * a.inv_phi_b + 1.0), 0.0), 1.0);
+    };
+    auto feq = [&](int k, double rho) {
+        const double cu = CXk(k) * a.u0x;
+        return WkD(k) * rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * a.u0x * a.u0x);
+    };
     for (int k = 0; k < 9; ++k) {
-        double v = 0.0;
+        double v;
         const int ty = y + CYk(k);
-        if (ty < 0 || ty >= a.ny) v = 6.0 * WkD(k) * rho * CXk(k) * a.uw[ty < 0 ? 0 : 1];
+        if (ty < 0 || ty >= a.ny) {
+            const double rho = rho_at(c);
+            v = feq(OPPk(k), rho) + 6.0 * WkD(k) * rho * CXk(k) * a.uw[ty < 0 ? 0 : 1];
+        } else {
+            v = feq(k, rho_at((long long)ty * a.nx + wrapx(x + CXk(k), a.nx)));
+        }
         Stor<T>::st(f, (long long)k * a.N + c, (float)v);
     }
     php[c] = (float)a.phi0[c];
@@ -192,6 +210,7 @@ StepArgs<T> make_args(slbm_domain* d, bool diag) {
     a.rec_prev = d->n == 0 ? d->recs + 3 : d->recs + ((d->n - 1) & 1);
     a.rec_out = diag ? d->recs + 2 : d->recs + (d->n & 1);
     a.first = d->n == 0;
+    a.level = d->n;
     if (diag && d->fields) {
         a.o_phi = d->fields; a.o_psi = d->fields + d->N; a.o_ux = d->fields + 2 * d->N;
         a.o_uy = d->fields + 3 * d->N; a.o_p = d->fields + 4 * d->N;
@@ -214,6 +233,10 @@ cudaError_t prepare_kernels() {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, true, false, false, true>, attr, st);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, false, true, false, true>, attr, st);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, true, true, false, true>, attr, st);
+        if constexpr (std::is_same<T, float>::value) {
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, false, false, false, false, true>, attr, sm);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, true, false, false, false, true>, attr, sm);
+        }
         return e;
     });
 }
@@ -226,6 +249,15 @@ cudaError_t launch_with(slbm_domain* d, const StepArgs<T>& a, bool diag) {
     // uniform density and viscosity (the common case) drop every density-gradient term
     const bool var = a.P.var_nu || a.P.rho_l != a.P.rho_g;
     const BatchArgs nb{};
+    if constexpr (std::is_same<T, float>::value) {
+        if (d->mms) {
+            static const TmaMaps none{};
+            const size_t sm = smem_bytes<T>();
+            if (diag) step_kernel<T, true, false, false, false, true><<<d->grid, NTHREADS, sm, d->stream>>>(a, nb, none);
+            else step_kernel<T, false, false, false, false, true><<<d->grid, NTHREADS, sm, d->stream>>>(a, nb, none);
+            return cudaGetLastError();
+        }
+    }
     if (d->tma) {
         const size_t sm = smem_bytes_tma<T>();
         const TmaMaps& m = d->maps[d->cur];
@@ -360,6 +392,7 @@ cudaError_t launch_init(slbm_domain* d, const double* phi0, const double* psi0) 
     a.eta_phi = d->p.eta_phi; a.eta_psi = d->p.eta_psi;
     a.rho_l = d->p.rho_l; a.rho_g = d->p.rho_g; a.inv_phi_b = 1.0 / d->phi_b;
     a.uw[0] = d->wall_u[0]; a.uw[1] = d->wall_u[1];
+    a.u0x = d->mms ? d->mms_u0x : 0.0;
     a.psi_on = d->p.psi_on != 0;
     const int c = d->cur;
     const unsigned blocks = (unsigned)((d->N + 255) / 256);
@@ -869,6 +902,25 @@ slbm_status slbm_load(slbm_domain* d, const char* path) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) return cuda_fail(d, e, "load");
     d->initialised = true;
+    return SLBM_OK;
+}
+
+slbm_status slbm_set_mms(slbm_domain* d, const slbm_mms* m) {
+    if (!d) return SLBM_EINVAL;
+    if (!m) {
+        d->mms = false;
+        d->mms_u0x = 0.0;
+        return SLBM_OK;
+    }
+    if (d->p.precision != SLBM_FP32) return fail(d, SLBM_EINVAL, "the manufactured-solution test runs in FP32 storage");
+    if (d->phys.var_nu || d->p.rho_l != d->p.rho_g) return fail(d, SLBM_EINVAL, "the test needs uniform density and viscosity");
+    if (!(m->dx > 0) || !(m->dt > 0)) return fail(d, SLBM_EINVAL, "dx and dt must be positive");
+    d->mms = true;
+    d->mms_u0x = m->u * m->dt / m->dx;
+    Phys& P = d->phys;
+    P.mms_a = (float)m->amplitude; P.mms_u = (float)m->u; P.mms_M = (float)m->M; P.mms_beta = (float)m->beta;
+    P.mms_kappa = (float)m->kappa; P.mms_kT = (float)m->kT; P.mms_W = (float)m->W;
+    P.mms_dx = (float)m->dx; P.mms_dt = (float)m->dt;
     return SLBM_OK;
 }
 

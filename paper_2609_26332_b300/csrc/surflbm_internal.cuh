@@ -34,6 +34,8 @@ struct slbm_domain {
     // caller-owned device workspace (slbm_create_domain_ext): every buffer is carved from
     // it in the order of slbm_workspace_bytes and nothing is allocated or freed
     bool tma = false;                 // the step stages through TMA boxes (maps of both sides)
+    bool mms = false;                 // manufactured-solution test (slbm_set_mms)
+    double mms_u0x = 0.0;             // its uniform lattice velocity (initial state)
     slbm::TmaMaps maps[2];
     bool ext = false;
     unsigned char* ws = nullptr;

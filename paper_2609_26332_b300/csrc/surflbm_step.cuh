@@ -124,6 +124,9 @@ struct Phys {
     float wSg[2], wSl[2], wS0g[2], wS0l[2], wLg[2], wLl[2];
     float psi_clamp;
     int psi_on, linear, target;
+    // manufactured-solution test (MMS kernels only): physical amplitude, advection speed,
+    // mobility, beta, kappa, k_B T, W, node spacing and time step
+    float mms_a, mms_u, mms_M, mms_beta, mms_kappa, mms_kT, mms_W, mms_dx, mms_dt;
     double Nd;                    // number of cells
     double M_phi_d, M_psi_d;
 };
@@ -151,6 +154,7 @@ struct StepArgs {
     const Rec* rec_prev;          // time level n-1 (zeros before the first step)
     Rec* rec_out;                 // time level n
     int first;                    // this is the first step after initialisation
+    long long level;              // time level of the populations the launch collides
     // DIAG outputs (device, double; may be null)
     double* o_phi; double* o_psi; double* o_ux; double* o_uy; double* o_p;
     Phys P;
@@ -309,6 +313,32 @@ __device__ __forceinline__ float wall_energy(float ph, float ps, int w, const Ph
     return -(P.wcos[w] + st_sg - st_sl) * gv + 0.5f * (st_sg + st_sl) + 0.5f * (P.wS0g[w] + P.wS0l[w]);
 }
 
+// Manufactured sources of Sec. 4.1 on the channel (lattice units per step) at node (gx, y)
+// and time level n: with X = 2 pi (x - u t), Y = 2 pi y and a = A e^{-t},
+//   phi^e = a sin X cos Y,  psi^e = 1/2 + 0.05 e^{-2t} cos X cos Y
+// are exact solutions of the phi and psi equations with the linear multipliers when
+//   S_phi = -phi^e + M mu_phi^e                       (the mean of mu_phi^e is 0)
+//   S_psi = -2 (psi^e - 1/2) + M (mu_psi^e - mean mu_psi^e),
+//   mean mu_psi^e = -beta (1 - a^2/2 + 9 a^4/64) + W a^2/8   (lambda_s = 0).
+__device__ __forceinline__ void mms_source(const Phys& P, long long n, int gx, int y, float& s_phi, float& s_psi) {
+    const float t = (float)n * P.mms_dt;
+    const float x = (float)gx * P.mms_dx, yy = ((float)y + 0.5f) * P.mms_dx;
+    float sX, cX;
+    sincospif(2.0f * (x - P.mms_u * t), &sX, &cX);
+    const float cY = cospif(2.0f * yy);
+    const float a = P.mms_a * expf(-t);
+    const float pe = a * sX * cY;
+    const float qe = 0.5f + 0.05f * expf(-2.0f * t) * cX * cY;
+    const float lap = -8.0f * 9.8696044f * pe;   // nabla^2 of the mode: -8 pi^2 phi^e
+    const float mu_phi = 4.0f * P.mms_beta * (1.0f - qe) * (pe * pe * pe - pe) + P.mms_W * qe * pe - P.mms_kappa * lap;
+    const float om = 1.0f - pe * pe;
+    const float mu_psi = P.mms_kT * logf(qe / (1.0f - qe)) - P.mms_beta * om * om + 0.5f * P.mms_W * pe * pe;
+    const float a2 = a * a;
+    const float mbar = -P.mms_beta * (1.0f - 0.5f * a2 + 9.0f / 64.0f * a2 * a2) + 0.125f * P.mms_W * a2;
+    s_phi = P.mms_dt * (-pe + P.mms_M * mu_phi);
+    s_psi = P.mms_dt * (-2.0f * (qe - 0.5f) + P.mms_M * (mu_psi - mbar));
+}
+
 // warp reduction of a float-float pair
 __device__ __forceinline__ ff warp_sum_ff(ff v) {
 #pragma unroll
@@ -441,10 +471,14 @@ __device__ __forceinline__ void static_for(F&& f) {
 // and the collide's flow populations, history and previous phi arrive by TMA boxes
 // (TmaStage), issued one iteration ahead by one thread; false: cp.async staging of the
 // stage-K rows and direct global loads in the collide (batches, odd or narrow grids).
-template <class T, bool DIAG, bool VARRHO, bool BATCH, bool TMA = false>
+// MMS = true: the manufactured-solution test of Sec. 4.1 on the channel (verification
+// only): no force acts on the flow, and the sources S_phi, S_psi that make the travelling
+// decaying modes exact are added to R_phi, R_psi (mms_source).
+template <class T, bool DIAG, bool VARRHO, bool BATCH, bool TMA = false, bool MMS = false>
 __global__ void __launch_bounds__(NTHREADS, 2)
     step_kernel(const StepArgs<T> A, const BatchArgs B, const __grid_constant__ TmaMaps M) {
     static_assert(!(TMA && BATCH), "the batch kernel stages with cp.async");
+    static_assert(!(MMS && (BATCH || VARRHO)), "the manufactured-solution test is a uniform-density single domain");
     extern __shared__ __align__(128) unsigned char smem[];
     int* sK = (int*)smem;
     float2* sMT = (float2*)(smem + SM_K);
@@ -906,8 +940,10 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         }
         const float lapN_psi = 6.0f * (lns - (1.0f - Wk(0)) * psi);
         wf_phi *= 6.0f; wf_psi *= 6.0f;
-        const float Fx = -phi * gmx - psi * gpx + P.Gx;
-        const float Fy = -phi * gmy - psi * gpy + P.Gy;
+        const float Fx = MMS ? 0.0f : -phi * gmx - psi * gpx + P.Gx;
+        const float Fy = MMS ? 0.0f : -phi * gmy - psi * gpy + P.Gy;
+        float mms_sphi = 0.0f, mms_spsi = 0.0f;
+        if (MMS && !DIAG) mms_source(P, A.level, gx, y, mms_sphi, mms_spsi);
         float chi = 0.f, rho = P.rho_l, inv_rho = inv_rho_l;
         if (VARRHO) {
             // grad rho = (rho_l - rho_g) grad chi over the clipped neighbour values
@@ -971,7 +1007,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         // -M_psi mu_psi - (M_psi lambda_s + M_0) Lap_N psi
         float Rf_psi = 0.0f;
         if (P.psi_on) {
-            Rf_psi = Stor<T>::rnd(-P.M_psi * MP(y, mc) - (P.M_psi * P.lambda_s + P.M_0) * lapN_psi);
+            Rf_psi = Stor<T>::rnd(-P.M_psi * MP(y, mc) - (P.M_psi * P.lambda_s + P.M_0) * lapN_psi + mms_spsi);
             acc[P_S3] = ff_add_f(acc[P_S3], Rf_psi);
         }
 
@@ -1052,7 +1088,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
             if (s == 0) {
                 // R_phi without the lambda^n term (deferred), with the kappa-weighted wall flux of the ghost-row closure
                 Rf = Stor<T>::rnd(P.M_phi * (-4.0f * P.beta * (1.0f - psi) * (phi * phi * phi - phi) -
-                                             P.W * psi * phi + P.kappa * wf_phi));
+                                             P.W * psi * phi + P.kappa * wf_phi) + mms_sphi);
             } else {
                 Rf = Rf_psi;
             }

@@ -44,3 +44,18 @@ def test_a_wrong_mean_potential_is_caught(monkeypatch):
     bad = mms.run(32, t_end=1.0)
     assert good[4] < 1e-13 and bad[4] > 5e-5
     assert bad[1] > 1.02 * good[1]
+
+
+def test_channel_form_second_order_and_conservation():
+    """The channel form of the test (u = (0.05, 0), both fields varying as cos 2 pi y so
+    that the neutral walls' zero-flux closure is exact for them), run through the full
+    Oracle with a prescribed velocity and the manufactured sources: second order in space
+    for phi and psi, sum psi to round-off."""
+    res = {n: mms.run_channel(n) for n in (16, 32, 64)}
+    for a, b in ((16, 32), (32, 64)):
+        o_phi = math.log2(res[a][0] / res[b][0])
+        o_psi = math.log2(res[a][1] / res[b][1])
+        print(f"channel dx 1/{a} -> 1/{b}: order phi {o_phi:.3f}, psi {o_psi:.3f}")
+        assert 1.9 < o_phi < 2.1 and 1.9 < o_psi < 2.1
+    for n, r in res.items():
+        assert r[3] < 1e-12, (n, r[3])
