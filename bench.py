@@ -153,16 +153,38 @@ def make_domain(case, stream):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """SM clock, power and clock-event (throttle) reasons sampled DURING the timed region:
+    an NVML polling thread every 5 ms (one sample is also taken at start and at stop, so a
+    region of a few milliseconds still has a record), else nvidia-smi at its 50 ms floor."""
 
+    REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown", 0x8),
+               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown", 0x40),
+               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown", 0x20),
+               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap", 0x4))
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
-        self.path = tempfile.mktemp(suffix=".csv")
-        self.proc = None
+    def __init__(self, index, period_s=0.005):
+        self.rows, self.proc, self.nvml, self.thread = [], None, None, None
+        self.period = period_s
         try:
+            import threading
+            import pynvml
+            pynvml.nvmlInit()
+            self.nvml = pynvml
+            self.h = self._handle(pynvml, index)
+            self.max_mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM))
+            self.bits = [(name, getattr(pynvml, attr, bit)) for name, attr, bit in self.REASONS]
+            self._sample()
+            self.halt = threading.Event()
+            self.thread = threading.Thread(target=self._loop, daemon=True)
+            self.thread.start()
+            return
+        except Exception:
+            self.nvml = None
+        try:
+            self.path = tempfile.mktemp(suffix=".csv")
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
@@ -170,7 +192,46 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
+    @staticmethod
+    def _handle(pynvml, index):
+        """The NVML handle of torch's device `index` (matched by PCI bus id: NVML counts every
+        GPU of the machine, CUDA only the visible ones)."""
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(index)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+            return pynvml.nvmlDeviceGetHandleByPciBusId(bus.encode())
+        except Exception:
+            return pynvml.nvmlDeviceGetHandleByIndex(index)
+
+    def _sample(self):
+        n = self.nvml
+        sm = float(n.nvmlDeviceGetClockInfo(self.h, n.NVML_CLOCK_SM))
+        try:
+            mask = n.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+        except Exception:
+            mask = n.nvmlDeviceGetCurrentClocksThrottleReasons(self.h)
+        self.rows.append((sm, [name for name, bit in self.bits if mask & bit]))
+
+    def _loop(self):
+        while not self.halt.wait(self.period):
+            try:
+                self._sample()
+            except Exception:
+                return
+
     def stop(self):
+        if self.nvml is not None:
+            self.halt.set()
+            self.thread.join(timeout=2)
+            try:
+                self._sample()
+            except Exception:
+                pass
+            sm = [r[0] for r in self.rows]
+            reasons = sorted({x for r in self.rows for x in r[1]})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(self.rows), "source": "nvml, 5 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -192,7 +253,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": "nvidia-smi, 50 ms"}
 
 
 def measured_peaks():

@@ -55,3 +55,29 @@ def test_kernel_hash_ignores_comments_and_layout():
     assert bench.code_only(a) == bench.code_only(b)
     assert bench.code_only("return 2 * x;") != bench.code_only("return 3 * x;")
     assert bench.state_bytes_per_cell("fp32") == 264 and bench.state_bytes_per_cell("bf16") == 152
+
+
+def test_clock_sampler_reads_nvml_reasons(monkeypatch):
+    """The clock record of the timed region from a fake NVML (reads only): median SM clock,
+    the device's maximum, and the throttle reasons seen in any sample by name."""
+    import types
+    import time
+    import bench
+    fake = types.SimpleNamespace(NVML_CLOCK_SM=0, nvmlClocksEventReasonHwSlowdown=0x8,
+                                 nvmlClocksEventReasonHwThermalSlowdown=0x40,
+                                 nvmlClocksEventReasonSwThermalSlowdown=0x20, nvmlClocksEventReasonSwPowerCap=0x4)
+    clocks = iter([1900.0, 2032.0, 2032.0] + [2032.0] * 10000)
+    masks = iter([0x0, 0x4, 0x1] + [0x0] * 10000)
+    fake.nvmlInit = lambda: None
+    fake.nvmlDeviceGetHandleByPciBusId = lambda bus: "h"
+    fake.nvmlDeviceGetHandleByIndex = lambda i: "h"
+    fake.nvmlDeviceGetMaxClockInfo = lambda h, kind: 2032
+    fake.nvmlDeviceGetClockInfo = lambda h, kind: next(clocks)
+    fake.nvmlDeviceGetCurrentClocksEventReasons = lambda h: next(masks)
+    monkeypatch.setitem(sys.modules, "pynvml", fake)
+    s = bench.ClockSampler(0, period_s=0.001)
+    time.sleep(0.02)
+    rec = s.stop()
+    assert rec["source"].startswith("nvml") and rec["samples"] >= 3
+    assert rec["sm_max_mhz"] == 2032 and rec["sm_mhz"] == 2032.0
+    assert rec["reasons"] == ["sw_power_cap"]   # 0x1 (idle) is not a throttle reason
