@@ -215,7 +215,7 @@ slbm_status slbm_read_totals(slbm_domain* d, slbm_totals* t);
  * queues the work on the stream.
  *
  * Scratch: the per-CTA partial sums, the completion counter and the result record live
- * in one file-scope static device array of SLBM_NOALLOC_SCRATCH_BYTES (about 99 KB),
+ * in one file-scope static device array of SLBM_NOALLOC_SCRATCH_BYTES (about 105 KB),
  * held by every GPU that loads this library until the process exits.  The array holds
  * at most SLBM_NOALLOC_MAX_CTAS CTAs of partials; a domain whose grid is larger is
  * rejected with SLBM_EINVAL (grids here are at most 2 CTAs per SM).  The first call on
@@ -228,7 +228,7 @@ slbm_status slbm_read_totals(slbm_domain* d, slbm_totals* t);
  * Errors: EINVAL (NULL domain, grid too large), ESTATE (fields never initialised),
  * ECUDA, EUNSTABLE (as slbm_read_totals). */
 #define SLBM_NOALLOC_MAX_CTAS 1024
-#define SLBM_NOALLOC_PARTS 12
+#define SLBM_NOALLOC_PARTS 13
 #define SLBM_NOALLOC_SCRATCH_BYTES (SLBM_NOALLOC_MAX_CTAS * SLBM_NOALLOC_PARTS * 8 + 256 + 256)
 slbm_status slbm_read_fields_noalloc(slbm_domain* d, double* phi, double* psi, double* ux, double* uy,
                                      double* p, slbm_totals* totals);

@@ -107,7 +107,9 @@ __global__ void __launch_bounds__(EX_THREADS) exact_multiplier_kernel(const Exac
         // target of the cubic: sum Q(phi^0) = 2 H0 - N (nonlinear), sum phi^0 = H0 (linear)
         const double target = P.linear ? r->H0 : 2.0 * r->H0 - P.Nd;
         const double p0 = s_tot[0] - target;
-        const double p1 = s_tot[1], p2 = s_tot[2], p3 = s_tot[3];
+        // linear constraint: the pull adds a M_phi lambda to every node in float-float, so the
+        // slope is N a M_phi exactly
+        const double p1 = P.linear ? P.Nd * r->a * P.M_phi_d : s_tot[1], p2 = s_tot[2], p3 = s_tot[3];
         // |f| at the rounding level of the difference that makes p0 also counts as a root
         // (a root at lambda ~ 0 never meets the relative step test)
         const double f_tol = 1e-14 * (fabs(s_tot[0]) + fabs(target));

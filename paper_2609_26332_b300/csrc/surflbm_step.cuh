@@ -33,7 +33,7 @@ constexpr int RING = 8;          // ring depth (rows)
 constexpr int KX = TX + 6;       // columns of the fixed-point ring (3-node halo)
 constexpr int PX = TX + 4;       // columns of the phi / psi ring (2-node halo)
 constexpr int MX = TX + 2;       // columns of the mu ring (1-node halo)
-constexpr int NPART = 12;        // doubles per block partial
+constexpr int NPART = 13;        // doubles per block partial
 
 // Raw source rows are staged with cp.async through a 16-byte aligned window of WW
 // columns starting at x0 - WOFF (covers the K-ring columns x0 - 3 .. x0 + TX + 2).
@@ -110,7 +110,7 @@ constexpr unsigned long long TMA_WAIT_NS = 2000000000ull;
 constexpr unsigned int ERR_TMA_WAIT = 1u;
 
 // indices of the block partials / reduced quantities
-enum { P_S1 = 0, P_S2, P_S3, P_Q, P_PHI, P_PSI, P_KIN, P_CLAMP, P_RANGE, P_EF, P_DPHI2, P_PHI2 };
+enum { P_S1 = 0, P_S2, P_S3, P_Q, P_PHI, P_PSI, P_KIN, P_CLAMP, P_RANGE, P_EF, P_DPHI2, P_PHI2, P_SR };
 
 struct Phys {
     float beta, kappa, lambda_s, W, kT, phi_b, inv_phi_b, M_phi, M_psi, M_0, eta_phi, eta_psi;
@@ -368,7 +368,15 @@ __device__ __forceinline__ Rec resolve_rec(const Phys& P, int first, const Rec* 
     r.H = P.linear ? r.phi_tot : 0.5 * P.Nd + 0.5 * r.Q;
     r.H0 = first ? r.H : rec_prev->H0;
     double lam = 0.0;
-    if (r.S2 > 0.0) {
+    if (P.linear && P.M_phi_d > 0.0) {
+        // linear constraint: M_phi lambda = -(sum of the stored free reaction terms) / N, which
+        // is the mean potential of Eq. eq15 with h' = 1 (the free terms sum to -M_phi sum
+        // mu_phi because the Neumann Laplacian of the lattice diffusion sums to zero); taken
+        // over the stored values, the multiplier's uniform term cancels them exactly and
+        // sum phi is conserved to float-float rounding, as sum psi is through mubar_psi
+        lam = -tot[P_SR] / (P.Nd * P.M_phi_d);
+        if (P.target) lam += (r.H0 - r.H) / (P.Nd * P.M_phi_d);
+    } else if (r.S2 > 0.0) {
         lam = r.S1 / r.S2;
         if (P.target && P.M_phi_d > 0.0) lam = (r.S1 + (r.H0 - r.H) / P.M_phi_d) / r.S2;
     }
@@ -524,6 +532,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     // deferred multiplier terms of time level n-1 (FP64 only here, once per piece)
     float inv_rho_l = 0.f, qcoef = 0.f, lam_half = 0.f;
     ff cuni = {0.f, 0.f}, mub_half = {0.f, 0.f};
+    ff clin = {0.f, 0.f}, lin_half = {0.f, 0.f};   // linear constraint: a M lambda and -M lambda / 2 (uniform)
     int nsets = 1;
     auto set_level = [&]() {
         const Rec rp = *rec_prev;
@@ -536,6 +545,11 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         const double hm = -0.5 * rp.mpsi_mubar;
         mub_half.hi = (float)hm;
         mub_half.lo = (float)(hm - (double)mub_half.hi);
+        const double cl = rp.a * P.M_phi_d * rp.lam, hl = -0.5 * P.M_phi_d * rp.lam;
+        clin.hi = (float)cl;
+        clin.lo = (float)(cl - (double)clin.hi);
+        lin_half.hi = (float)hl;
+        lin_half.lo = (float)(hl - (double)lin_half.hi);
         nsets = P.psi_on ? 2 : 1;
     };
     int range = 0;
@@ -656,7 +670,9 @@ __global__ void __launch_bounds__(NTHREADS, 2)
             const float2 mv = ((const float2*)(row + ST::D_ROW))[s * WW + col];
             ff mt = {mv.x, mv.y};
             if (s == 0) {
-                if (qcoef != 0.0f) {
+                if (P.linear) {
+                    mt = ff_add(mt, clin);
+                } else if (qcoef != 0.0f) {
                     const float php = ((const float*)(row + ST::D_ROW + ST::M_ROW))[col];
                     mt = ff_add_f(mt, __fmul_rn(qcoef, hprime(php, P)));
                 }
@@ -704,7 +720,9 @@ __global__ void __launch_bounds__(NTHREADS, 2)
                                                           : (s == 0 ? TS::O_MOM0 : TS::O_MOM1))))[col];
             ff mt = {mv.x, mv.y};
             if (s == 0) {
-                if (qcoef != 0.0f) {
+                if (P.linear) {
+                    mt = ff_add(mt, clin);
+                } else if (qcoef != 0.0f) {
                     const float php = ((const float*)(sTma + (side ? TS::O_SPHP : TS::O_PHPK)))[col];
                     mt = ff_add_f(mt, __fmul_rn(qcoef, hprime(php, P)));
                 }
@@ -1005,6 +1023,11 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         // - M_0 Lap_N psi, written with the mu_psi of stage MU at this node (which holds the
         // same logarithm and adsorption terms with -lambda_s Lap_G psi):
         // -M_psi mu_psi - (M_psi lambda_s + M_0) Lap_N psi
+        // free reaction term of phi (R_phi without the lambda^n term, which is deferred), with
+        // the kappa-weighted wall flux of the ghost-row closure, rounded to storage
+        const float Rf_phi = Stor<T>::rnd(P.M_phi * (-4.0f * P.beta * (1.0f - psi) * (phi * phi * phi - phi) -
+                                                     P.W * psi * phi + P.kappa * wf_phi) + mms_sphi);
+        if (P.linear) acc[P_SR] = ff_add_f(acc[P_SR], Rf_phi);
         float Rf_psi = 0.0f;
         if (P.psi_on) {
             Rf_psi = Stor<T>::rnd(-P.M_psi * MP(y, mc) - (P.M_psi * P.lambda_s + P.M_0) * lapN_psi + mms_spsi);
@@ -1085,22 +1108,18 @@ __global__ void __launch_bounds__(NTHREADS, 2)
             const ff cff = s == 0 ? phff : psff;
             float Rf;
             ff dR;
-            if (s == 0) {
-                // R_phi without the lambda^n term (deferred), with the kappa-weighted wall flux of the ghost-row closure
-                Rf = Stor<T>::rnd(P.M_phi * (-4.0f * P.beta * (1.0f - psi) * (phi * phi * phi - phi) -
-                                             P.W * psi * phi + P.kappa * wf_phi) + mms_sphi);
-            } else {
-                Rf = Rf_psi;
-            }
+            Rf = s == 0 ? Rf_phi : Rf_psi;
             // dR = R + (R - R_prev)/2 minus the multiplier part of R_prev; exact in float-float
             // for the surfactant (its total is conserved to round-off), plain float for phi
             if (first) {
                 dR = {Rf, 0.0f};
-            } else if (s == 0) {
+            } else if (s == 0 && !P.linear) {
                 dR = {1.5f * Rf - 0.5f * Rp_phi - lam_half * hprime(php_self, P), 0.0f};
             } else {
-                const ff t = two_sum(Rf, -Rp_psi);
-                dR = ff_add(ff_add_f(ff_scale_pow2(t, 0.5f), Rf), mub_half);
+                // exact in float-float where the total is conserved: the surfactant, and phi
+                // under the linear constraint
+                const ff t = two_sum(Rf, -(s == 0 ? Rp_phi : Rp_psi));
+                dR = ff_add(ff_add_f(ff_scale_pow2(t, 0.5f), Rf), s == 0 ? lin_half : mub_half);
             }
             const ff mstar = ff_add(cff, dR);
             const float isc = s == 0 ? isc_phi : isc_psi;
