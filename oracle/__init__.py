@@ -16,6 +16,8 @@ phase-field model for surfactant contact line dynamics with solid adsorption"):
 * ``analysis`` - contact angle, zero-level-set area, free energy (Sec. 4)
 * ``warmstart`` - the warm-start network (convolutions, adjoints, loss) in float64
 * ``mms``      - manufactured-solution convergence harness of the scalar equations (Sec. 4.1)
+* ``lattice3d``, ``lbm3d`` - the same scheme in three dimensions on D3Q19 (Sec. 2.3 states
+  the model for d = 2, 3), single relaxation time, x and z periodic, y walls
 
 Pins (tests that tie it to something other than itself) live in
 ``tests/test_oracle_*.py``.  Parts without such a pin are marked "parity unpinned"
@@ -24,5 +26,6 @@ in their docstrings.
 
 from .params import OracleParams, Wall, derive
 from .lbm import Oracle
+from .lbm3d import Oracle3D
 
-__all__ = ["OracleParams", "Wall", "derive", "Oracle"]
+__all__ = ["OracleParams", "Wall", "derive", "Oracle", "Oracle3D"]

@@ -165,23 +165,24 @@ class Oracle:
 
     def _wall_ghosts(self, phi, psi):
         """Ghost rows (bottom at j = -1, top at j = ny) from Eq. boundary."""
+        return [self._ghost_values(w, phi[row], psi[row]) for w, row in ((0, 0), (1, self.ny - 1))]
+
+    def _ghost_values(self, w, ph, ps):
+        """Ghost values beyond wall w from the wall-row values ph, ps (any shape):
+        phi_G = phi_0 - (df_w/dphi)/kappa, psi_G = psi_0 - (df_w/dpsi)/lambda_s."""
         d, p = self.d, self.p
-        out = []
-        for w, row in ((0, 0), (1, self.ny - 1)):
-            ph, ps = phi[row], psi[row]
-            psc = self._clamp(ps) if p.psi_on else ps
-            L = np.log1p(-psc)
-            t_sg, t_sl, on_sg, on_sl = self._wall_tension_factors(w, L)
-            # f_w = (1/2 - g) sigma_sg + (1/2 + g) sigma_sl with sigma_s,a = sigma_s,a,0 (1 + t_a)
-            # and sigma_sg,0 - sigma_sl,0 written as sigma cos(theta0) (Eq. fw0, Eq. langmuir)
-            dfdphi = -(d.wall_cos[w] + d.wall_sg0[w] * t_sg - d.wall_sl0[w] * t_sl) * self._gprime(ph)
-            g = self._g(ph)
-            dfdpsi = -((0.5 - g) * d.wall_sg0[w] * p.walls[w].beta_sg * on_sg
-                       + (0.5 + g) * d.wall_sl0[w] * p.walls[w].beta_sl * on_sl) / (1.0 - psc)
-            phiG = ph - dfdphi / d.kappa if d.kappa > 0 else ph.copy()
-            psiG = ps - dfdpsi / d.lambda_s if (d.lambda_s > 0 and p.psi_on) else ps.copy()
-            out.append((phiG, psiG))
-        return out
+        psc = self._clamp(ps) if p.psi_on else ps
+        L = np.log1p(-psc)
+        t_sg, t_sl, on_sg, on_sl = self._wall_tension_factors(w, L)
+        # f_w = (1/2 - g) sigma_sg + (1/2 + g) sigma_sl with sigma_s,a = sigma_s,a,0 (1 + t_a)
+        # and sigma_sg,0 - sigma_sl,0 written as sigma cos(theta0) (Eq. fw0, Eq. langmuir)
+        dfdphi = -(d.wall_cos[w] + d.wall_sg0[w] * t_sg - d.wall_sl0[w] * t_sl) * self._gprime(ph)
+        g = self._g(ph)
+        dfdpsi = -((0.5 - g) * d.wall_sg0[w] * p.walls[w].beta_sg * on_sg
+                   + (0.5 + g) * d.wall_sl0[w] * p.walls[w].beta_sl * on_sl) / (1.0 - psc)
+        phiG = ph - dfdphi / d.kappa if d.kappa > 0 else ph.copy()
+        psiG = ps - dfdpsi / d.lambda_s if (d.lambda_s > 0 and p.psi_on) else ps.copy()
+        return phiG, psiG
 
     def _rates(self, main, others, shape, flow):
         """Per-cell diagonal of S (9, ny, nx); zeros in ``others`` mean 'equal to main'."""
