@@ -592,6 +592,73 @@ def run_conv(args, rank, world, dist):
         }))
 
 
+# the three-dimensional step (D3Q19): 3 x 19 populations read and written plus 8 history
+# values read and written, FP32
+BYTES_PER_CELL_3D = 2 * (3 * 19 + 8) * 4
+
+
+def run_3d(args, rank, world, dist):
+    """The three-dimensional extension: a hemispherical surfactant drop on the bottom wall
+    under a sliding top wall (the shear configuration's physics), nx x ny x nz =
+    256 x 128 x 256 (8.4 M cells, the cell count of the 2D benchmark), three launches per
+    step, CUDA events on the library's stream."""
+    import torch
+    from paper_2609_26332_b300 import binding as B, inputs
+    nx, ny, nz = args.nx3, args.ny3, args.nz3
+    cells = nx * ny * nz
+    R = 0.375 * ny
+    pb = inputs.bulk_phi(0.02, SHEAR_EX)
+    phi0, psi0 = inputs.sessile_drop3d(nx, ny, nz, R, 4.0, phi_b=pb, psi0=0.02)
+    stream = torch.cuda.current_stream()
+    p = B.default_params(nx, ny, psi_b=0.02, sigma=SHEAR_SIGMA, Ex=SHEAR_EX, Pi=SHEAR_PI)
+    d = B.Domain3D(p, nz, stream=stream)
+    d.set_wall(0, 90.0, 0.5, 0.0, 0.0)
+    d.set_wall(1, 90.0, 0.0, 0.0, 0.01)
+    d.init_fields(phi0, psi0)
+    d.step(args.warmup)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = ranks.max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    clocks = sampler.stop() if sampler else None
+    tot = d.read_totals(check=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d.init_fields(phi0, psi0)
+    d.step(args.steps)
+    out = d.read_fields()
+    e2e_s = ranks.max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    if rank == 0:
+        peak, kind = measured_peaks()
+        per_step = ms / 1e3 / args.steps
+        achieved = BYTES_PER_CELL_3D * cells / per_step / 1e9
+        print(json.dumps({
+            "metric": "coupled-step MLUPS (3D)", "value": world * cells * args.steps / (ms / 1e3) / 1e6,
+            "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"3D shear drop {nx}x{ny}x{nz} R={R:.0f} fp32 (D3Q19)", "cells": cells,
+                       "parallelism": f"replicas{world}",
+                       "l2": f"state {cells * 2 * (19 + 36 + 4 + 8 + 8) * 4 / 1e9:.2f} GB >> 126 MB L2, no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_kind": kind, "bytes_per_cell": BYTES_PER_CELL_3D,
+                         "kernels": ["moments3d", "potentials3d", "collide3d"]},
+            "e2e": {"value": world * cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": 16 * cells / args.steps, "d2h_bytes_per_step": 48 * cells / args.steps},
+            "gpu_launches": 3 * args.steps, "clocks": clocks,
+            "totals": {"psi_total": tot["psi_total"], "lambda_phi": tot["lambda_phi"],
+                       "range_count": tot["range_count"],
+                       "phi_range": [float(out["phi"].min()), float(out["phi"].max())]},
+        }))
+    d.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -606,7 +673,10 @@ def main():
                          "exact root of the discrete constraint (one extra reduction pass per step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="shear", choices=["shear", "drop1000", "batch", "warmstart", "shear-track",
-                                                             "conv"])
+                                                             "conv", "3d"])
+    ap.add_argument("--nx3", type=int, default=256)
+    ap.add_argument("--ny3", type=int, default=128)
+    ap.add_argument("--nz3", type=int, default=256)
     ap.add_argument("--track-steps", type=int, default=50000)
     ap.add_argument("--ws-train", type=int, default=4096)
     ap.add_argument("--ws-eval", type=int, default=256)
@@ -636,8 +706,9 @@ def main():
     from paper_2609_26332_b300 import build as _build
     _build.build()
     from paper_2609_26332_b300 import binding as B
-    if args.workload in ("batch", "warmstart", "shear-track", "conv"):
-        {"batch": run_batch, "warmstart": run_warmstart, "shear-track": run_shear_track, "conv": run_conv}[args.workload](
+    if args.workload in ("batch", "warmstart", "shear-track", "conv", "3d"):
+        {"batch": run_batch, "warmstart": run_warmstart, "shear-track": run_shear_track, "conv": run_conv,
+         "3d": run_3d}[args.workload](
             args, rank, world, dist)
         if dist:
             dist.destroy_process_group()

@@ -94,6 +94,22 @@ def _load():
                  "slbm_read_fields", "slbm_read_totals", "slbm_create_domain_ext", "slbm_save", "slbm_load",
                  "slbm_set_mms"):
         getattr(L, name).restype = ctypes.c_int
+    # three-dimensional extension
+    L.slbm3d_create_domain.argtypes = [ctypes.POINTER(Params), i, vp, ctypes.POINTER(vp)]
+    L.slbm3d_set_walls.argtypes = [vp, i, d, d, d, d]
+    L.slbm3d_init_fields.argtypes = [vp, dp, dp]
+    L.slbm3d_step.argtypes = [vp, ll]
+    L.slbm3d_read_fields.argtypes = [vp, dp, dp, dp, dp, dp, dp]
+    L.slbm3d_read_totals.argtypes = [vp, ctypes.POINTER(Totals)]
+    L.slbm3d_device_bytes.argtypes = [vp]
+    L.slbm3d_device_bytes.restype = ctypes.c_size_t
+    L.slbm3d_destroy.argtypes = [vp]
+    L.slbm3d_destroy.restype = None
+    L.slbm3d_last_error.argtypes = [vp]
+    L.slbm3d_last_error.restype = ctypes.c_char_p
+    for name in ("slbm3d_create_domain", "slbm3d_set_walls", "slbm3d_init_fields", "slbm3d_step",
+                 "slbm3d_read_fields", "slbm3d_read_totals"):
+        getattr(L, name).restype = ctypes.c_int
     # batches
     L.slbm_create_batch.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(WallSpec), i, vp, ctypes.POINTER(vp)]
     L.slbm_batch_init_fields.argtypes = [vp, i, dp, dp]
@@ -301,6 +317,79 @@ class Domain:
 
 def version():
     return lib.slbm_version().decode()
+
+
+class Domain3D:
+    """A three-dimensional domain (D3Q19, include/surflbm3d.h) on the current CUDA device:
+    nx x ny x nz nodes, x and z periodic, walls below y = 0 and above y = ny - 1; fields are
+    numpy arrays of shape (nz, ny, nx)."""
+
+    def __init__(self, params, nz, stream=None):
+        self._h = ctypes.c_void_p()
+        self.nx, self.ny, self.nz = params.nx, params.ny, int(nz)
+        st = lib.slbm3d_create_domain(ctypes.byref(params), int(nz), _stream_handle(stream), ctypes.byref(self._h))
+        if st != SLBM_OK:
+            raise SlbmError(st, lib.slbm3d_last_error(None).decode())
+        self.params = params
+
+    def _check(self, st):
+        if st != SLBM_OK:
+            raise SlbmError(st, lib.slbm3d_last_error(self._h).decode())
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def set_wall(self, wall, theta0_deg=90.0, beta_sg=0.0, beta_sl=0.0, u_x=0.0):
+        self._check(lib.slbm3d_set_walls(self._h, int(wall), float(theta0_deg), float(beta_sg), float(beta_sl),
+                                         float(u_x)))
+
+    def init_fields(self, phi, psi=None):
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        if phi.shape != self.shape:
+            raise ValueError("phi must have shape (nz, ny, nx)")
+        if psi is not None:
+            psi = np.ascontiguousarray(psi, dtype=np.float64)
+            if psi.shape != self.shape:
+                raise ValueError("psi must have shape (nz, ny, nx)")
+        self._check(lib.slbm3d_init_fields(self._h, _dptr(phi), _dptr(psi)))
+
+    def step(self, n=1):
+        self._check(lib.slbm3d_step(self._h, int(n)))
+
+    def read_fields(self, which=("phi", "psi", "ux", "uy", "uz", "p")):
+        out = {k: np.empty(self.shape, dtype=np.float64) for k in which}
+        ptrs = [_dptr(out.get(k)) for k in ("phi", "psi", "ux", "uy", "uz", "p")]
+        self._check(lib.slbm3d_read_fields(self._h, *ptrs))
+        return out
+
+    def read_totals(self, check=True):
+        t = Totals()
+        st = lib.slbm3d_read_totals(self._h, ctypes.byref(t))
+        if check:
+            self._check(st)
+        return {name: getattr(t, name) for name, _ in Totals._fields_}
+
+    @property
+    def device_bytes(self):
+        return int(lib.slbm3d_device_bytes(self._h))
+
+    def close(self):
+        if self._h:
+            lib.slbm3d_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Batch:

@@ -2,7 +2,7 @@
 
 Usage: ``python -m paper_2609_26332_b300.build [--verbose]``.  The library holds
 the CUDA kernels and the C ABI declared in ``include/surflbm.h`` and
-``include/surflbm_ws.h``.
+``include/surflbm_ws.h`` and ``include/surflbm3d.h``.
 """
 import os
 import subprocess
@@ -12,7 +12,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libsurflbm.so")
-SOURCES = ["surflbm_api.cu", "surflbm_batch.cu", "surflbm_exact.cu", "ws_net.cu"]
+SOURCES = ["surflbm_api.cu", "surflbm_batch.cu", "surflbm_exact.cu", "surflbm3d.cu", "ws_net.cu"]
 HEADERS = ["surflbm_device.cuh", "surflbm_step.cuh", "surflbm_internal.cuh", "ws_tc.cuh", "ws_conv.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP32 denormals flushed, approximate FP32 division and square root: the few divisions and
@@ -32,7 +32,7 @@ def needs_build():
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", h) for h in ("surflbm.h", "surflbm_ws.h")]
+    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", h) for h in ("surflbm.h", "surflbm_ws.h", "surflbm3d.h")]
     return any(os.path.getmtime(p) > t for p in deps)
 
 

@@ -529,6 +529,11 @@ void fill_totals(const slbm_domain* d, const Rec& r, slbm_totals* t) {
 
 }  // namespace
 
+// parameter checks and derivation shared with the three-dimensional domain
+std::string slbm_validate_params(const slbm_params* p) { return validate(p); }
+void slbm_derive_phys(slbm_domain* d) { derive(d); }
+void slbm_wall_phys(slbm_domain* d, int w) { set_wall_phys(d, w); }
+
 extern "C" {
 
 void slbm_default_params(slbm_params* p, int nx, int ny) {

@@ -43,6 +43,12 @@ struct slbm_domain {
     std::string err = "no error";
 };
 
+// Parameter checks (empty string: valid), derivation of the model constants and Phys, and
+// one wall's Phys entries (surflbm_api.cu); also used by the three-dimensional domain.
+std::string slbm_validate_params(const slbm_params* p);
+void slbm_derive_phys(slbm_domain* d);
+void slbm_wall_phys(slbm_domain* d, int w);
+
 // The diagnostic pass of the current level into d->fields (phi, psi, ux, uy, p planes),
 // reduced with the domain's own partials; queued on the domain's stream.
 slbm_status diag_into_fields(slbm_domain* d);

@@ -71,6 +71,32 @@ def free_drop(nx, ny, R, eps, xc=None, yc=None, phi_b=1.0, psi0=0.0):
     return phi_b * np.tanh(2.0 * phi_b * (R - r) / eps), np.full((ny, nx), float(psi0))
 
 
+def sessile_drop3d(nx, ny, nz, R, eps, xc=None, zc=None, phi_b=1.0, psi0=0.0, psi_noise=0.0, seed=DEFAULT_SEED):
+    """Hemispherical drop of radius R centred on the bottom wall at (xc, 0, zc), arrays
+    [z][y][x] (node (i, j, l) at x = i, y = j + 1/2, z = l): phi = phi_b tanh(2 phi_b (R - r)
+    / eps); psi = psi0 + U(-psi_noise, psi_noise)."""
+    xc = nx / 2.0 if xc is None else xc
+    zc = nz / 2.0 if zc is None else zc
+    z = np.arange(nz, dtype=np.float64)[:, None, None]
+    y = np.arange(ny, dtype=np.float64)[None, :, None] + 0.5
+    x = np.arange(nx, dtype=np.float64)[None, None, :]
+    r = np.sqrt((x - xc) ** 2 + y ** 2 + (z - zc) ** 2)
+    phi = phi_b * np.tanh(2.0 * phi_b * (R - r) / eps)
+    psi = np.full((nz, ny, nx), float(psi0))
+    if psi_noise > 0:
+        psi = psi + psi_noise * (2.0 * uniform(seed, nx * ny * nz).reshape(nz, ny, nx) - 1.0)
+    return phi, psi
+
+
+def free_drop3d(nx, ny, nz, R, eps, phi_b=1.0, psi0=0.0):
+    """Spherical drop at the centre of the box, arrays [z][y][x]."""
+    z = np.arange(nz, dtype=np.float64)[:, None, None]
+    y = np.arange(ny, dtype=np.float64)[None, :, None] + 0.5
+    x = np.arange(nx, dtype=np.float64)[None, None, :]
+    r = np.sqrt((x - nx / 2.0) ** 2 + (y - ny / 2.0) ** 2 + (z - nz / 2.0) ** 2)
+    return phi_b * np.tanh(2.0 * phi_b * (R - r) / eps), np.full((nz, ny, nx), float(psi0))
+
+
 def ellipse(nx, ny, a, b, eps, phi_b=1.0):
     """Ellipse with semi-axes a (x) and b (y) centred in the box; the signed distance
     to the ellipse is approximated by the first-order formula F / |grad F| with

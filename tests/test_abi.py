@@ -15,14 +15,14 @@ def _declared():
         if h.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", h)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names += re.findall(r"\b(slbm_[a-z_0-9]+)\s*\(", txt)
+            names += re.findall(r"\b(slbm(?:3d)?_[a-z_0-9]+)\s*\(", txt)
     return sorted(set(names))
 
 
 def test_library_exports_every_declared_symbol():
     from paper_2609_26332_b300 import binding as B
     names = _declared()
-    assert "slbm_step" in names and "slbm_create_domain" in names
+    assert "slbm_step" in names and "slbm_create_domain" in names and "slbm3d_step" in names
     for n in names:
         assert hasattr(B.lib, n), n
     assert "sm_103a" in B.version()
@@ -70,3 +70,19 @@ def test_warm_start_entry_points_validate_before_touching_the_gpu():
     assert B.lib.slbm_conv3x3_input_grad(fake, fake, None, fake, 1, 8, 8, 24, 32, None) == B.SLBM_EINVAL
     assert B.lib.slbm_conv3x3_weight_grad(fake, fake, fake, 1, 8, 8, 32, 256, None) == B.SLBM_EINVAL
     assert B.lib.slbm_ws_param_count(None) == 0
+
+
+def test_3d_extension_rejects_what_it_does_not_cover():
+    """The three-dimensional domain refuses, before touching the GPU, the modes it does not
+    implement: 16-bit storage, MRT rates, variable density, the exact multiplier, nz < 1."""
+    from paper_2609_26332_b300 import binding as B
+    for bad in (dict(precision=B._PREC["bf16"]), dict(rho_l=10.0), dict(multiplier=B.EXACT), dict(tau_f_gas=0.6)):
+        q = B.default_params(16, 8, **bad)
+        with pytest.raises(B.SlbmError) as e:
+            B.Domain3D(q, 8)
+        assert e.value.status == B.SLBM_EINVAL
+    q = B.default_params(16, 8, mrt_g=(0.0, 1.2, 0.0, 0.0))
+    with pytest.raises(B.SlbmError):
+        B.Domain3D(q, 8)
+    with pytest.raises(B.SlbmError):
+        B.Domain3D(B.default_params(16, 8), 0)
