@@ -66,7 +66,7 @@ EXACT_BYTES_PER_CELL = {"fp32": 44, "fp16": 28, "bf16": 28}
 # DRAM bytes (read + write) per step_kernel launch on the 4096 x 2048 shear workload from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the
 # step kernel's code (comments stripped) and float flags: a changed kernel reports null until re-measured.
-TRAFFIC = {"0639687a74fedb47": {"fp32": 3.13e9, "fp16": 2.10e9, "bf16": 2.10e9}}
+TRAFFIC = {"1d3ecfad1cdb6412": {"fp32": 3.128e9}}
 
 
 def code_only(src):
@@ -152,10 +152,57 @@ def make_domain(case, stream):
     return d
 
 
+class _NvmlLib:
+    """The few read-only NVML queries the clock sampler needs, through the driver's
+    libnvidia-ml directly (ctypes), for hosts without the Python NVML package."""
+
+    NVML_CLOCK_SM = 1
+
+    def __init__(self):
+        import ctypes
+        self.ct = ctypes
+        self.L = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.L.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+
+    def _handle(self, fn, arg):
+        h = self.ct.c_void_p()
+        if fn(arg, self.ct.byref(h)) != 0:
+            raise RuntimeError("no NVML handle")
+        return h
+
+    def nvmlDeviceGetHandleByPciBusId(self, bus):
+        return self._handle(self.L.nvmlDeviceGetHandleByPciBusId_v2, self.ct.c_char_p(bus))
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        return self._handle(self.L.nvmlDeviceGetHandleByIndex_v2, self.ct.c_uint(i))
+
+    def _uint(self, fn, h, kind):
+        v = self.ct.c_uint()
+        if fn(h, self.ct.c_int(kind), self.ct.byref(v)) != 0:
+            raise RuntimeError("NVML clock query failed")
+        return v.value
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        return self._uint(self.L.nvmlDeviceGetClockInfo, h, kind)
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        return self._uint(self.L.nvmlDeviceGetMaxClockInfo, h, kind)
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.ct.c_ulonglong()
+        fn = getattr(self.L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.L.nvmlDeviceGetCurrentClocksThrottleReasons
+        if fn(h, self.ct.byref(v)) != 0:
+            raise RuntimeError("NVML reasons query failed")
+        return v.value
+
+
 class ClockSampler:
-    """SM clock, power and clock-event (throttle) reasons sampled DURING the timed region:
-    an NVML polling thread every 5 ms (one sample is also taken at start and at stop, so a
-    region of a few milliseconds still has a record), else nvidia-smi at its 50 ms floor."""
+    """SM clock and clock-event (throttle) reasons sampled DURING the timed region: an NVML
+    polling thread every 5 ms (the Python NVML package, else the driver's libnvidia-ml
+    through ctypes; one sample is also taken at start and at stop, so a region of a few
+    milliseconds still has a record), else nvidia-smi at its 50 ms floor."""
 
     REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown", 0x8),
                ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown", 0x40),
@@ -170,8 +217,11 @@ class ClockSampler:
         self.period = period_s
         try:
             import threading
-            import pynvml
-            pynvml.nvmlInit()
+            try:
+                import pynvml
+                pynvml.nvmlInit()
+            except ImportError:
+                pynvml = _NvmlLib()
             self.nvml = pynvml
             self.h = self._handle(pynvml, index)
             self.max_mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM))

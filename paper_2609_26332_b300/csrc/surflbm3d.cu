@@ -113,16 +113,38 @@ __device__ __forceinline__ void sfor(F&& f) {
     }
 }
 
+// Every cell once: block b takes a contiguous range of row segments (a segment is up to T3
+// consecutive x of one row (y, z); segment-major order), fixed and deterministic, and steps
+// through it incrementing y and z, so no integer division is done per cell.
+template <class F>
+__device__ __forceinline__ void for_cells(const Grid3& G, F&& body) {
+    const int nseg = (G.nx + T3 - 1) / T3;
+    const int rows = G.ny * G.nz;
+    const long long items = (long long)rows * nseg;
+    const long long lo = items * blockIdx.x / gridDim.x, hi = items * (blockIdx.x + 1) / gridDim.x;
+    if (lo >= hi) return;
+    int seg = (int)(lo / rows), row = (int)(lo - (long long)seg * rows);
+    int y = row % G.ny, z = row / G.ny;
+    for (long long it = lo; it < hi; ++it) {
+        const int x = seg * T3 + (int)threadIdx.x;
+        if (x < G.nx) body((long long)row * G.nx + x, x, y, z);
+        if (++row == rows) {
+            row = y = z = 0;
+            ++seg;
+        } else if (++y == G.ny) {
+            y = 0;
+            ++z;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ moments3d
 __global__ void __launch_bounds__(T3) moments3d(const Args3 A) {
     const Grid3 G = A.g;
     const float scl[2] = {(float)(1u << SFIX_PHI), 2147483648.0f};
     const float isc[2] = {1.0f / scl[0], 1.0f / scl[1]};
     const int nsets = A.P.psi_on ? 2 : 1;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < G.N; c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % G.nx);
-        const long long r = c / G.nx;
-        const int y = (int)(r % G.ny), z = (int)(r / G.ny);
+    for_cells(G, [&](long long c, int x, int y, int z) {
         for (int s = 0; s < 2; ++s) {
             float2* out = s == 0 ? A.phi : A.psi;
             if (s >= nsets) {
@@ -145,7 +167,7 @@ __global__ void __launch_bounds__(T3) moments3d(const Args3 A) {
             const ff v = ff_add(ff_add({m.x, m.y}, fixed_to_ff(dh, isc[s])), fixed_to_ff((int)(diff - dh), isc[s]));
             out[c] = make_float2(v.hi, v.lo);
         }
-    }
+    });
 }
 
 // ------------------------------------------------------------------ potentials3d
@@ -173,10 +195,7 @@ __global__ void __launch_bounds__(T3) potentials3d(const Args3 A, int diag) {
 #pragma unroll
     for (int q = 0; q < NPART; ++q) acc[q] = {0.f, 0.f};
     float clamps = 0.f;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < G.N; c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % G.nx);
-        const long long r = c / G.nx;
-        const int y = (int)(r % G.ny), z = (int)(r / G.ny);
+    for_cells(G, [&](long long c, int x, int y, int z) {
         const float2 pc = A.phi[c], sc = A.psi[c];
         const float phi = pc.x, psi = sc.x;
         float lgp = 0.f, lgs = 0.f, lnp = 0.f, lns = 0.f;
@@ -219,7 +238,7 @@ __global__ void __launch_bounds__(T3) potentials3d(const Args3 A, int diag) {
         acc[P_Q] = ff_add_f(acc[P_Q], 1.5f * u - 0.5f * u * u * u);
         acc[P_PHI] = ff_add(acc[P_PHI], {pc.x, pc.y});
         acc[P_PSI] = ff_add(acc[P_PSI], {sc.x, sc.y});
-    }
+    });
     acc[P_CLAMP] = {clamps, 0.f};
     __shared__ double s_blk[NPART], s_tot[NPART];
     __shared__ bool s_last;
@@ -248,7 +267,7 @@ __device__ __forceinline__ ff uniform_part(double cn, double cp, int first) {
 }
 
 template <bool DIAG>
-__global__ void __launch_bounds__(T3) collide3d(const Args3 A) {
+__global__ void __launch_bounds__(T3, 2) collide3d(const Args3 A) {
     const Grid3 G = A.g;
     const Phys& P = A.P;
     const long long N = G.N;
@@ -261,10 +280,7 @@ __global__ void __launch_bounds__(T3) collide3d(const Args3 A) {
     const ff uphi = uniform_part(P.M_phi_d * rn.lam, P.M_phi_d * rp.lam, A.first);
     float kin = 0.f;
     int range = 0;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % G.nx);
-        const long long r = c / G.nx;
-        const int y = (int)(r % G.ny), z = (int)(r / G.ny);
+    for_cells(G, [&](long long c, int x, int y, int z) {
         const float2 pcf = A.phi[c], scf = A.psi[c];
         const float phi = pcf.x, psi = scf.x;
         // flow pull with halfway bounce-back (moving wall along x)
@@ -316,7 +332,7 @@ __global__ void __launch_bounds__(T3) collide3d(const Args3 A) {
             if (A.o[3]) A.o[3][c] = uy;
             if (A.o[4]) A.o[4][c] = uz;
             if (A.o[5]) A.o[5][c] = pres;
-            continue;
+            return;
         }
         // flow BGK collision with F_{i,1} (uniform density: w_i c_i . F / c_s^2)
         {
@@ -391,7 +407,7 @@ __global__ void __launch_bounds__(T3) collide3d(const Args3 A) {
             hs[(long long)(3 + 3 * s) * N] = s == 0 ? phuy : psuy;
             hs[(long long)(4 + 3 * s) * N] = s == 0 ? phuz : psuz;
         }
-    }
+    });
     if constexpr (DIAG) {
         // kinetic energy and the range flag of the diagnostic level into its record
         ff acc[NPART];
@@ -472,7 +488,7 @@ struct slbm3d_domain {
     int cur = 0;
     long long n = 0;
     bool initialised = false;
-    int grid = 1;
+    int grid[3] = {1, 1, 1};    // moments3d, potentials3d, collide3d: resident blocks (persistent)
     float* f[2] = {nullptr, nullptr};
     float* g[2] = {nullptr, nullptr};
     float* h[2] = {nullptr, nullptr};
@@ -532,15 +548,15 @@ Args3 make_args3(slbm3d_domain* d, bool diag) {
 cudaError_t launch_level(slbm3d_domain* d, bool diag) {
     Args3 a = make_args3(d, diag);
     cudaStream_t st = d->core.stream;
-    moments3d<<<d->grid, T3, 0, st>>>(a);
-    potentials3d<<<d->grid, T3, 0, st>>>(a, diag ? 1 : 0);
+    moments3d<<<d->grid[0], T3, 0, st>>>(a);
+    potentials3d<<<d->grid[1], T3, 0, st>>>(a, diag ? 1 : 0);
     if (diag) {
         if (d->out) {
             for (int q = 0; q < 6; ++q) a.o[q] = d->out + (long long)q * d->G.N;
         }
-        collide3d<true><<<d->grid, T3, 0, st>>>(a);
+        collide3d<true><<<d->grid[1], T3, 0, st>>>(a);
     } else {
-        collide3d<false><<<d->grid, T3, 0, st>>>(a);
+        collide3d<false><<<d->grid[2], T3, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -578,8 +594,18 @@ slbm_status slbm3d_create_domain(const slbm_params* p, int nz, void* stream, slb
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long blocks = (d->G.N + T3 - 1) / T3;
-    d->grid = (int)(blocks < 4LL * sms ? blocks : 4LL * sms);
+    // persistent grids: the resident blocks of each kernel, at most one block per row segment
+    const long long segs = (long long)((p->nx + T3 - 1) / T3) * p->ny * nz;
+    const void* fns[3] = {(const void*)moments3d, (const void*)potentials3d, (const void*)collide3d<false>};
+    int maxgrid = 1;
+    for (int k = 0; k < 3; ++k) {
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fns[k], T3, 0) != cudaSuccess || per < 1) per = 1;
+        const long long g = (long long)per * sms;
+        d->grid[k] = (int)(g < segs ? g : segs);
+        if (d->grid[k] > maxgrid) maxgrid = d->grid[k];
+    }
+    cudaGetLastError();
     const size_t N = (size_t)d->G.N;
     cudaError_t e = cudaSuccess;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
@@ -592,7 +618,7 @@ slbm_status slbm3d_create_domain(const slbm_params* p, int nz, void* stream, slb
     if (e == cudaSuccess) e = alloc3(d, &d->hist, 8 * N * 4);
     if (e == cudaSuccess) e = alloc3(d, &d->mom, 2 * N * sizeof(float2));
     if (e == cudaSuccess) e = alloc3(d, &d->pot, 4 * N * 4);
-    if (e == cudaSuccess) e = alloc3(d, &d->partials, (size_t)d->grid * NPART * sizeof(double));
+    if (e == cudaSuccess) e = alloc3(d, &d->partials, (size_t)maxgrid * NPART * sizeof(double));
     if (e == cudaSuccess) e = alloc3(d, &d->counter, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = alloc3(d, &d->recs, 4 * sizeof(Rec));
     if (e == cudaSuccess) e = cudaMemsetAsync(d->counter, 0, 2 * sizeof(unsigned int), d->core.stream);
