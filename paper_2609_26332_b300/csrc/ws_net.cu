@@ -5,9 +5,13 @@
 #include "surflbm_internal.cuh"
 #include "surflbm_ws.h"
 #include "ws_conv.cuh"
+#include "ws_conv_tma.cuh"
+
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -439,8 +443,111 @@ cudaError_t conv_attrs() {
     });
 }
 
+// ---- tensor-memory-accelerator convolution (ws_conv_tma.cuh)
+PFN_cuTensorMapEncodeTiled_v12000 tma_encode_fn() {
+    static std::once_flag flag;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(flag, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// channels per K block of the TMA convolution: 64, 32 or 16 (0: not supported)
+int tma_kc(int C) { return C % 64 == 0 ? 64 : (C % 32 == 0 ? 32 : (C % 16 == 0 ? 16 : 0)); }
+
+// pixel tile Wt x Ht x Bt = 128 that tiles the B x H x W grid exactly, or false
+bool tma_tile(int B, int H, int W, int& Wt, int& Ht, int& Bt) {
+    Wt = W < 128 ? W : 128;
+    if (W % Wt || 128 % Wt) return false;
+    const int rest = 128 / Wt;
+    Ht = H < rest ? H : rest;
+    if (H % Ht || rest % Ht) return false;
+    Bt = rest / Ht;
+    return B % Bt == 0;
+}
+
+constexpr int TC_SMEM_BUDGET = 110 * 1024;   // two CTAs per SM
+
+cudaError_t tconv_attrs() {
+    static slbm::PerDeviceOnce once;
+    return once([] {
+        // the ring (at most TC_SMEM_BUDGET bytes: 2 stages of the widest tiles take 96 KB) and
+        // 1 KB of alignment slack
+        return cudaFuncSetAttribute(conv_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BUDGET + 1024);
+    });
+}
+
+// the TMA convolution when the shapes allow it (true), else false (nothing launched)
+bool launch_tconv(const bf16* x, const bf16* w, const float* bias, const bf16* mask, bf16* y, int B, int H, int W,
+                  int C, int N, int relu, unsigned int* err, cudaStream_t st, cudaError_t* res) {
+    int Wt, Ht, Bt;
+    const int KC = tma_kc(C);
+    auto enc = tma_encode_fn();
+    if (!enc || KC == 0 || N % 16 || N < 16 || N > 256 || !tma_tile(B, H, W, Wt, Ht, Bt)) return false;
+    const CUtensorMapSwizzle sw = KC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                           : (KC == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+    CUtensorMap mx, mw;
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const cuuint64_t xd[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t xs[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+    const cuuint32_t xb[4] = {(cuuint32_t)KC, (cuuint32_t)Wt, (cuuint32_t)Ht, (cuuint32_t)Bt};
+    const cuuint64_t wd[2] = {(cuuint64_t)9 * C, (cuuint64_t)N};
+    const cuuint64_t ws_[1] = {(cuuint64_t)9 * C * 2};
+    const cuuint32_t wb[2] = {(cuuint32_t)KC, (cuuint32_t)N};
+    if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x), xd, xs, xb, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(w), wd, ws_, wb, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    cudaError_t e = tconv_attrs();
+    if (e != cudaSuccess) {
+        *res = e;
+        return true;
+    }
+    TConvArgs a;
+    a.bias = bias; a.mask = mask; a.y = y;
+    a.B = B; a.H = H; a.W = W; a.C = C; a.N = N; a.relu = relu;
+    a.Wt = Wt; a.Ht = Ht; a.Bt = Bt; a.KC = KC;
+    a.a_bytes = 128u * (uint32_t)KC * 2u;
+    a.b_bytes = (((uint32_t)N * (uint32_t)KC * 2u) + 1023u) & ~1023u;
+    const uint32_t sb = a.a_bytes + a.b_bytes;
+    int stages = (int)(TC_SMEM_BUDGET / sb);
+    stages = stages > TC_MAX_STAGES ? TC_MAX_STAGES : stages;
+    if (stages < 2) return false;
+    a.stages = stages;
+    a.err = err;
+    const size_t smem = (size_t)stages * sb + 1024;
+    // persistent grid: the CTAs that fit at once (two accumulators of N columns each in the
+    // 512 columns of tensor memory, and the shared-memory ring), at most one per tile
+    int dev = 0, sms = 148, smem_sm = 233472;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    // per CTA: the dynamic ring, ~1 KB of static barriers and the 1 KB the runtime reserves
+    int per = (int)((size_t)smem_sm / (smem + 2048));
+    const int by_tmem = (int)(512u / (2u * tmem_cols_for(N)));
+    if (per > by_tmem) per = by_tmem;
+    if (per < 1) per = 1;
+    const long long tiles = (long long)B * H * W / 128;
+    const unsigned grid = (unsigned)(tiles < (long long)per * sms ? tiles : (long long)per * sms);
+    conv_tma_kernel<<<grid, TC_THREADS, smem, st>>>(mx, mw, a);
+    *res = cudaGetLastError();
+    return true;
+}
+
 cudaError_t launch_mk(const bf16* x, const bf16* w, const float* bias, const bf16* mask, bf16* y, int B, int H, int W,
                       int C, int N, int relu, unsigned int* err, cudaStream_t st) {
+    cudaError_t te = cudaSuccess;
+    if (launch_tconv(x, w, bias, mask, y, B, H, W, C, N, relu, err, st, &te)) return te;
     cudaError_t e = conv_attrs();
     if (e != cudaSuccess) return e;
     MKArgs a{x, w, bias, mask, y, B, H, W, C, N, relu, err};

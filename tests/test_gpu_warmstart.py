@@ -39,6 +39,14 @@ CONV_CASES = [
     (1, 12, 20, 192, 64),
     (1, 4, 40, 128, 128),
     (3, 7, 11, 64, 64),
+    # pixel counts that the 128-pixel tiles of the TMA kernel cover exactly, each channel
+    # block width (16, 32, 64) and tile shape (row segment, several rows, several images)
+    (2, 8, 128, 16, 32),
+    (1, 16, 256, 96, 32),
+    (4, 4, 8, 128, 128),
+    (2, 32, 64, 192, 64),
+    (1, 8, 32, 256, 256),
+    (2, 4, 64, 64, 16),
 ]
 
 
