@@ -81,7 +81,7 @@ def kernel_hash():
     import hashlib
     from paper_2609_26332_b300 import build as _b
     h = hashlib.sha256()
-    for f in ("surflbm_step.cuh", "surflbm_device.cuh"):
+    for f in ("surflbm_step.cuh", "surflbm_step_tile.inc", "surflbm_device.cuh"):
         h.update(code_only(open(os.path.join(_b.CSRC, f)).read()).encode())
     h.update(" ".join(_b.FLOAT_FLAGS).encode())
     return h.hexdigest()[:16]
@@ -402,6 +402,7 @@ def run_batch(args, rank, world, dist):
     cache = args.tiling_cache or os.path.join(tempfile.gettempdir(), "surflbm_tiling.json")
     band_rows, ctas = b.autotune(cache)
     b.set_tiling(band_rows, ctas, args.graph_steps)
+    strip_width = b.tiling()[0]
     b.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -464,7 +465,8 @@ def run_batch(args, rank, world, dist):
                                    f"{sizes[-1][0]}x{sizes[-1][1]}, theta0 U[30,150], psi0 U[0.005,0.05], "
                                    f"adsorption U[0,1], {args.precision}",
                        "instances": len(specs_all), "cells": cells_all, "rank0_share": [lo, hi],
-                       "band_rows": band_rows, "ctas_per_sm": ctas,
+                       "strip_width": strip_width, "band_rows": band_rows, "ctas_per_sm": ctas,
+                       "cells_per_thread_per_piece": band_rows // 4,
                        "graph_steps": args.graph_steps, "parallelism": f"instance shares x{world}",
                        "l2": f"state {cells * 2 * BYTES_PER_CELL[args.precision] / 2 / 1e9:.1f} GB >> 126 MB L2, no flush"},
             "per_instance_launches": {"value": per_inst, "unit": "MLUPS", "steps": k_inst,

@@ -262,15 +262,29 @@ slbm_status slbm_batch_init_fields(slbm_batch* b, int idx, const double* phi, co
 /* As slbm_batch_init_fields with phi, psi in device memory (slbm_init_fields_device). */
 slbm_status slbm_batch_init_fields_device(slbm_batch* b, int idx, const double* phi, const double* psi);
 
-/* Tiling of the tile queue: each instance is cut into strips of 64 columns and bands of
- * about band_rows rows (>= 8); ctas_per_sm (1 or 2) resident CTAs per SM take pieces
- * from the queue; graph_steps launches per captured graph. */
+/* Tiling of the tile queue: each instance is cut into strips of the strip width (64
+ * columns by default, see slbm_batch_set_strip_width) and bands of about band_rows rows
+ * (>= 8), so a piece is a tile of width x band_rows cells and each thread of the CTA
+ * marching it (4 rows per step of its pipeline) handles band_rows / 4 cells of it;
+ * ctas_per_sm resident CTAs per SM (1 or 2 with 64-column strips, 1 to 3 with 32) take
+ * pieces from the queue; graph_steps launches per captured graph. */
 slbm_status slbm_batch_set_tiling(slbm_batch* b, int band_rows, int ctas_per_sm, int graph_steps);
 
-/* Times the candidate tilings (band_rows 16..256, 1 or 2 CTAs per SM) on this batch and
- * keeps the fastest; the choice is read from / appended to the JSON file cache_path
- * (may be NULL), keyed by precision, instance count, total cells and the size list.
- * The timed steps are real steps of every active instance (8 per candidate). */
+/* Strip width of the tile queue: 64 (the step kernel with 256 threads per CTA) or 32 (its
+ * 32-column instance, 128 threads per CTA, more pieces and smaller shared-memory rings for
+ * narrow instances at twice the relative halo).  Same method; fields agree to FP32 rounding
+ * (the tiling fixes the order of the per-thread partial sums).  Clamps ctas_per_sm to the
+ * width's maximum.  EINVAL for other widths. */
+slbm_status slbm_batch_set_strip_width(slbm_batch* b, int width);
+
+/* The current tiling: strip width, band rows, resident CTAs per SM (any may be NULL). */
+slbm_status slbm_batch_get_tiling(const slbm_batch* b, int* strip_width, int* band_rows, int* ctas_per_sm);
+
+/* Times the candidate tilings (strip width 64 or 32 x band_rows 16..256 x every allowed
+ * CTAs-per-SM count) on this batch and keeps the fastest; the choice is read from /
+ * appended to the JSON file cache_path (may be NULL) as [band_rows, ctas_per_sm,
+ * strip_width], keyed by precision, instance count, total cells and the size list.  The
+ * timed steps are real steps of every active instance (8 per candidate). */
 slbm_status slbm_batch_autotune(slbm_batch* b, const char* cache_path, int* band_rows_out, int* ctas_out);
 
 /* nsteps time steps of every active instance (asynchronous on the batch's stream). */

@@ -114,6 +114,8 @@ def _load():
     L.slbm_create_batch.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(WallSpec), i, vp, ctypes.POINTER(vp)]
     L.slbm_batch_init_fields.argtypes = [vp, i, dp, dp]
     L.slbm_batch_set_tiling.argtypes = [vp, i, i, i]
+    L.slbm_batch_set_strip_width.argtypes = [vp, i]
+    L.slbm_batch_get_tiling.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     L.slbm_batch_autotune.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(i), ctypes.POINTER(i)]
     L.slbm_batch_step.argtypes = [vp, ll]
     L.slbm_batch_run_to_equilibrium.argtypes = [vp, d, ll, i, ctypes.POINTER(ll)]
@@ -121,6 +123,7 @@ def _load():
     L.slbm_batch_read_fields.argtypes = [vp, i, dp, dp, dp, dp, dp]
     L.slbm_batch_read_totals.argtypes = [vp, i, ctypes.POINTER(Totals)]
     for name in ("slbm_create_batch", "slbm_batch_init_fields", "slbm_batch_set_tiling", "slbm_batch_autotune",
+                 "slbm_batch_set_strip_width", "slbm_batch_get_tiling",
                  "slbm_batch_step", "slbm_batch_run_to_equilibrium", "slbm_batch_step_instance",
                  "slbm_batch_read_fields", "slbm_batch_read_totals"):
         getattr(L, name).restype = ctypes.c_int
@@ -424,6 +427,15 @@ class Batch:
 
     def set_tiling(self, band_rows=64, ctas_per_sm=2, graph_steps=32):
         self._check(lib.slbm_batch_set_tiling(self._h, int(band_rows), int(ctas_per_sm), int(graph_steps)))
+
+    def set_strip_width(self, width):
+        self._check(lib.slbm_batch_set_strip_width(self._h, int(width)))
+
+    def tiling(self):
+        """(strip width, band rows, resident CTAs per SM) of the tile queue."""
+        w, br, cs = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib.slbm_batch_get_tiling(self._h, ctypes.byref(w), ctypes.byref(br), ctypes.byref(cs)))
+        return w.value, br.value, cs.value
 
     def autotune(self, cache_path=None):
         br, cs = ctypes.c_int(), ctypes.c_int()

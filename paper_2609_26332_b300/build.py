@@ -13,7 +13,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libsurflbm.so")
 SOURCES = ["surflbm_api.cu", "surflbm_batch.cu", "surflbm_exact.cu", "surflbm3d.cu", "ws_net.cu"]
-HEADERS = ["surflbm_device.cuh", "surflbm_step.cuh", "surflbm_internal.cuh", "ws_tc.cuh", "ws_conv.cuh", "ws_conv_tma.cuh"]
+HEADERS = ["surflbm_device.cuh", "surflbm_step.cuh", "surflbm_step_tile.inc", "surflbm_internal.cuh", "ws_tc.cuh", "ws_conv.cuh", "ws_conv_tma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP32 denormals flushed, approximate FP32 division and square root: the few divisions and
 # roots of the step are not on the conserved paths (moments are float-float sums and the

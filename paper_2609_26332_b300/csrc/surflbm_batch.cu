@@ -1,9 +1,19 @@
 // Batches: many independent domains (instances of uneven sizes and parameters) stepped
 // together, one launch of the persistent tile-queue kernel per time step, K steps
 // replayed from a captured CUDA graph, converged instances retired between graph
-// replays, and the tiling (band height x resident CTAs per SM) chosen by a timing
-// autotuner whose choices are cached in a JSON file.
+// replays, and the tiling (strip width x band height, i.e. the cells each thread marches
+// per piece, x resident CTAs per SM) chosen by a timing autotuner whose choices are cached
+// in a JSON file.
 #include "surflbm_internal.cuh"
+
+// the step kernel with 32-column strips (128 threads per CTA), the batch's second tile shape
+namespace slbm {
+namespace w32 {
+#define SLBM_TILE_TX 32
+#include "surflbm_step_tile.inc"
+#undef SLBM_TILE_TX
+}  // namespace w32
+}  // namespace slbm
 
 #include <algorithm>
 #include <chrono>
@@ -59,13 +69,18 @@ template <class T>
 cudaError_t prepare_batch_kernels() {
     static PerDeviceOnce once;
     return once([] {
-        const int sm = (int)smem_bytes<T>();
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<T, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(step_kernel<T, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        const int sm = (int)smem_bytes<T>(), sm32 = (int)w32::smem_bytes<T>();
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<T, false, false, true>, attr, sm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, false, true, true>, attr, sm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(w32::step_kernel<T, false, false, true>, attr, sm32);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(w32::step_kernel<T, false, true, true>, attr, sm32);
         return e;
     });
 }
+
+// resident CTAs per SM the strip width allows at most (shared memory and registers)
+int max_ctas_per_sm(int width) { return width == 32 ? 3 : 2; }
 
 }  // namespace
 
@@ -80,8 +95,8 @@ slbm_status bcuda(slbm_batch* b, cudaError_t e, const char* what) {
     return bfail(b, SLBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-int pieces_of(const slbm_domain* d, int band_rows, int* bands_out) {
-    const int strips = (d->p.nx + TX - 1) / TX;
+int pieces_of(const slbm_domain* d, int width, int band_rows, int* bands_out) {
+    const int strips = (d->p.nx + width - 1) / width;
     int bands = (d->p.ny + band_rows - 1) / band_rows;
     if (bands < 1) bands = 1;
     if (bands_out) *bands_out = bands;
@@ -118,9 +133,9 @@ slbm_status build_tables(slbm_batch* b) {
         I.P = d->phys;
         if (!b->active[i]) continue;
         int bands = 1;
-        const int np = pieces_of(d, b->band_rows, &bands);
+        const int np = pieces_of(d, b->strip_width, b->band_rows, &bands);
         I.npieces = np;
-        const int strips = (d->p.nx + TX - 1) / TX;
+        const int strips = (d->p.nx + b->strip_width - 1) / b->strip_width;
         int slot = 0;
         // band-major order inside an instance: neighbouring strips of one band are queued together
         for (int bd = 0; bd < bands; ++bd) {
@@ -171,10 +186,16 @@ cudaError_t launch_batch(slbm_batch* b) {
     ba.queue = b->d_queue;
     ba.done = b->d_queue + 1;
     ba.G = b->d_G;
-    const size_t sm = smem_bytes<T>();
     static const TmaMaps none{};
-    if (b->var) step_kernel<T, false, true, true><<<b->nctas, NTHREADS, sm, b->stream>>>(a, ba, none);
-    else step_kernel<T, false, false, true><<<b->nctas, NTHREADS, sm, b->stream>>>(a, ba, none);
+    if (b->strip_width == 32) {
+        const size_t sm = w32::smem_bytes<T>();
+        if (b->var) w32::step_kernel<T, false, true, true><<<b->nctas, w32::NTHREADS, sm, b->stream>>>(a, ba, none);
+        else w32::step_kernel<T, false, false, true><<<b->nctas, w32::NTHREADS, sm, b->stream>>>(a, ba, none);
+    } else {
+        const size_t sm = smem_bytes<T>();
+        if (b->var) step_kernel<T, false, true, true><<<b->nctas, NTHREADS, sm, b->stream>>>(a, ba, none);
+        else step_kernel<T, false, false, true><<<b->nctas, NTHREADS, sm, b->stream>>>(a, ba, none);
+    }
     return cudaGetLastError();
 }
 
@@ -383,7 +404,7 @@ slbm_status slbm_create_batch(const slbm_params* params, const slbm_wall_spec* w
         }
         b->var = b->var || d->phys.var_nu || d->phys.rho_l != d->phys.rho_g;
         b->bytes += d->bytes;
-        b->max_pieces[i] = pieces_of(d, 8, nullptr);   // the smallest band the tiling allows
+        b->max_pieces[i] = pieces_of(d, 32, 8, nullptr);   // the narrowest strips and smallest band the tiling allows
         b->part_off[i] = part_total;
         part_total += (size_t)b->max_pieces[i] * NPART;
         b->snap_off[i] = snap_total;
@@ -436,12 +457,30 @@ slbm_status slbm_batch_init_fields_device(slbm_batch* b, int idx, const double* 
 
 slbm_status slbm_batch_set_tiling(slbm_batch* b, int band_rows, int ctas_per_sm, int graph_steps) {
     if (!b) return SLBM_EINVAL;
-    if (band_rows < 8 || ctas_per_sm < 1 || ctas_per_sm > 2 || graph_steps < 1)
-        return bfail(b, SLBM_EINVAL, "need band_rows >= 8, ctas_per_sm in {1, 2}, graph_steps >= 1");
+    if (band_rows < 8 || ctas_per_sm < 1 || ctas_per_sm > max_ctas_per_sm(b->strip_width) || graph_steps < 1)
+        return bfail(b, SLBM_EINVAL, "need band_rows >= 8, ctas_per_sm in 1 .. 2 (3 for 32-column strips), graph_steps >= 1");
     b->band_rows = band_rows;
     b->ctas_per_sm = ctas_per_sm;
     b->graph_steps = graph_steps;
     b->tables_valid = false;
+    return SLBM_OK;
+}
+
+slbm_status slbm_batch_set_strip_width(slbm_batch* b, int width) {
+    if (!b) return SLBM_EINVAL;
+    if (width != 32 && width != 64) return bfail(b, SLBM_EINVAL, "strip width must be 32 or 64");
+    b->strip_width = width;
+    if (b->ctas_per_sm > max_ctas_per_sm(width)) b->ctas_per_sm = max_ctas_per_sm(width);
+    b->tables_valid = false;
+    drop_graph(b);
+    return SLBM_OK;
+}
+
+slbm_status slbm_batch_get_tiling(const slbm_batch* b, int* strip_width, int* band_rows, int* ctas_per_sm) {
+    if (!b) return SLBM_EINVAL;
+    if (strip_width) *strip_width = b->strip_width;
+    if (band_rows) *band_rows = b->band_rows;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
     return SLBM_OK;
 }
 
@@ -487,52 +526,61 @@ slbm_status slbm_batch_run_to_equilibrium(slbm_batch* b, double tol, long long m
 slbm_status slbm_batch_autotune(slbm_batch* b, const char* cache_path, int* band_rows_out, int* ctas_out) {
     if (!b) return SLBM_EINVAL;
     const std::string sig = signature(b);
-    // cached choice?
+    auto apply = [&](int width, int br, int cs) {
+        slbm_batch_set_strip_width(b, width);
+        slbm_batch_set_tiling(b, br, cs, b->graph_steps);
+        if (band_rows_out) *band_rows_out = br;
+        if (ctas_out) *ctas_out = cs;
+    };
+    // cached choice?  lines "key": [band_rows, ctas_per_sm, strip_width] (a two-entry line:
+    // 64-column strips)
     if (cache_path) {
         std::ifstream in(cache_path);
         std::string line;
         while (std::getline(in, line)) {
-            int br = 0, cs = 0;
+            int br = 0, cs = 0, width = 64;
             char key[256] = {0};
-            if (std::sscanf(line.c_str(), " \"%255[^\"]\": [%d, %d]", key, &br, &cs) == 3 && sig == key) {
-                slbm_batch_set_tiling(b, br, cs, b->graph_steps);
-                if (band_rows_out) *band_rows_out = br;
-                if (ctas_out) *ctas_out = cs;
+            const int got = std::sscanf(line.c_str(), " \"%255[^\"]\": [%d, %d, %d]", key, &br, &cs, &width);
+            if (got >= 3 && sig == key && (width == 32 || width == 64)) {
+                apply(width, br, cs);
                 return SLBM_OK;
             }
         }
     }
+    // candidates: strip width (the tile's x extent) x band height (its y extent, i.e. the
+    // band_rows / 4 cells each thread marches per piece) x resident CTAs per SM
     const int bands[] = {16, 32, 64, 128, 256};
     double best = INFINITY;
-    int best_br = b->band_rows, best_cs = b->ctas_per_sm;
+    int best_w = b->strip_width, best_br = b->band_rows, best_cs = b->ctas_per_sm;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int keep_graph = b->graph_steps;
-    for (int cs = 1; cs <= 2; ++cs) {
-        for (int br : bands) {
-            slbm_batch_set_tiling(b, br, cs, keep_graph);
-            slbm_status s = run_steps(b, 2);    // build tables, warm up
-            if (s) return s;
-            cudaEventRecord(e0, b->stream);
-            s = run_steps(b, 6);
-            if (s) return s;
-            cudaEventRecord(e1, b->stream);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                best_br = br;
-                best_cs = cs;
+    for (int width : {64, 32}) {
+        slbm_batch_set_strip_width(b, width);
+        for (int cs = 1; cs <= max_ctas_per_sm(width); ++cs) {
+            for (int br : bands) {
+                slbm_batch_set_tiling(b, br, cs, b->graph_steps);
+                slbm_status s = run_steps(b, 2);    // build tables, warm up
+                if (s) return s;
+                cudaEventRecord(e0, b->stream);
+                s = run_steps(b, 6);
+                if (s) return s;
+                cudaEventRecord(e1, b->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    best_w = width;
+                    best_br = br;
+                    best_cs = cs;
+                }
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    slbm_batch_set_tiling(b, best_br, best_cs, keep_graph);
-    if (band_rows_out) *band_rows_out = best_br;
-    if (ctas_out) *ctas_out = best_cs;
+    apply(best_w, best_br, best_cs);
     if (cache_path) {
         // append the choice (a JSON object, one key per line)
         std::vector<std::string> lines;
@@ -545,7 +593,7 @@ slbm_status slbm_batch_autotune(slbm_batch* b, const char* cache_path, int* band
         for (auto& l : lines)
             if (!l.empty() && l.back() == ',') l.pop_back();
         char buf[320];
-        std::snprintf(buf, sizeof(buf), "  \"%s\": [%d, %d]", sig.c_str(), best_br, best_cs);
+        std::snprintf(buf, sizeof(buf), "  \"%s\": [%d, %d, %d]", sig.c_str(), best_br, best_cs, best_w);
         lines.push_back(buf);
         std::ofstream outf(cache_path);
         outf << "{\n";

@@ -70,6 +70,7 @@ struct slbm_batch {
     std::vector<long long> G0;        // batch step at each instance's time level 0
     long long G = 0;                  // host mirror of the device step counter
     int band_rows = 64, ctas_per_sm = 2, graph_steps = 32;
+    int strip_width = 64;             // columns per strip: 64 (256 threads) or 32 (128 threads)
     // device tables
     slbm::InstDesc* d_inst = nullptr;
     slbm::Piece* d_pieces = nullptr;

@@ -43,10 +43,11 @@ CASES = [
 ]
 
 
-def _batch(cases, band_rows=16, ctas=2, graph_steps=16, precision="fp32"):
+def _batch(cases, band_rows=16, ctas=2, graph_steps=16, precision="fp32", width=64):
     from paper_2609_26332_b300 import binding as B
     params, walls = _params_and_walls(cases, precision)
     b = B.Batch(params, walls)
+    b.set_strip_width(width)
     b.set_tiling(band_rows, ctas, graph_steps)
     for i, c in enumerate(cases):
         phi, psi = fields0(c)
@@ -54,11 +55,12 @@ def _batch(cases, band_rows=16, ctas=2, graph_steps=16, precision="fp32"):
     return b
 
 
-@pytest.mark.parametrize("band_rows,ctas", [(16, 2), (64, 1)])
-def test_batch_matches_instances_stepped_alone(band_rows, ctas):
+@pytest.mark.parametrize("band_rows,ctas,width", [(16, 2, 64), (64, 1, 64), (16, 3, 32), (40, 2, 32)])
+def test_batch_matches_instances_stepped_alone(band_rows, ctas, width):
     _cuda()
     steps = 100   # graph replays plus single launches
-    with _batch(CASES, band_rows, ctas, graph_steps=16) as b:
+    with _batch(CASES, band_rows, ctas, graph_steps=16, width=width) as b:
+        assert b.tiling() == (width, band_rows, ctas)
         b.step(steps)
         for i, c in enumerate(CASES):
             with domain_for(c) as d:
@@ -76,10 +78,11 @@ def test_batch_matches_instances_stepped_alone(band_rows, ctas):
                 assert abs(tb["psi_total"] - ts["psi_total"]) <= 1e-12 * ts["psi_total"]
 
 
-def test_batch_instances_match_oracle():
+@pytest.mark.parametrize("width", [64, 32])
+def test_batch_instances_match_oracle(width):
     _cuda()
     sel = [CASES[1], CASES[2]]
-    with _batch(sel, band_rows=16, ctas=2, graph_steps=8) as b:
+    with _batch(sel, band_rows=16, ctas=2, graph_steps=8, width=width) as b:
         b.step(150)
         for i, c in enumerate(sel):
             o = oracle_for(c)
@@ -127,9 +130,11 @@ def test_autotune_writes_and_reuses_cache(tmp_path):
     cache = str(tmp_path / "tiling.json")
     with _batch(CASES[:3]) as b:
         br, cs = b.autotune(cache)
-        assert br in (16, 32, 64, 128, 256) and cs in (1, 2)
+        w = b.tiling()[0]
+        assert br in (16, 32, 64, 128, 256) and w in (32, 64) and 1 <= cs <= (3 if w == 32 else 2)
         data = json.load(open(cache))
-        assert list(data.values()) == [[br, cs]]
-        assert b.autotune(cache) == (br, cs)        # read back from the cache
+        assert list(data.values()) == [[br, cs, w]]
+        b.set_strip_width(96 - w)                   # the other width, then the cached choice again
+        assert b.autotune(cache) == (br, cs) and b.tiling() == (w, br, cs)
         b.step(10)
         assert b.read_totals(0)["range_count"] == 0
