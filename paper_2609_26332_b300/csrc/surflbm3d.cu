@@ -74,6 +74,39 @@ struct Grid3 {
     __device__ __forceinline__ int wz(int z) const { return z < 0 ? z + nz : (z >= nz ? z - nz : z); }
 };
 
+// The neighbours of one cell as offsets from its index, set once per cell: x and z wrap
+// periodically, y stays in the own row where x + c leaves [0, ny) (the caller decides what a
+// wall link means there: mirror, ghost, bounce-back or specular partner).
+struct Nbr {
+    long long c;
+    int ox[3], oz[3], oym, oyp;
+    bool ylo, yhi;
+    __device__ __forceinline__ Nbr(const Grid3& G, long long c_, int x, int y, int z) : c(c_) {
+        const int pl = G.nx * G.ny;
+        ox[0] = x == 0 ? G.nx - 1 : -1;
+        ox[1] = 0;
+        ox[2] = x == G.nx - 1 ? 1 - G.nx : 1;
+        oz[0] = z == 0 ? (G.nz - 1) * pl : -pl;
+        oz[1] = 0;
+        oz[2] = z == G.nz - 1 ? (1 - G.nz) * pl : pl;
+        ylo = y == 0;
+        yhi = y == G.ny - 1;
+        oym = ylo ? 0 : -G.nx;
+        oyp = yhi ? 0 : G.nx;
+    }
+    // index of the node at (x + DX, y + DY, z + DZ), y kept where it would leave the channel
+    template <int DX, int DY, int DZ>
+    __device__ __forceinline__ long long at() const {
+        int o = ox[DX + 1] + oz[DZ + 1];
+        if constexpr (DY < 0) o += oym;
+        if constexpr (DY > 0) o += oyp;
+        return c + o;
+    }
+    // does y + DY leave [0, ny)?
+    template <int DY>
+    __device__ __forceinline__ bool out() const { return (DY < 0 && ylo) || (DY > 0 && yhi); }
+};
+
 struct Args3 {
     Grid3 g;
     const float* f_in; const float* g_in; const float2* gm_in; const float* h_in; const float2* hm_in;
@@ -95,14 +128,9 @@ struct Args3 {
 // a link whose source lies beyond a y-wall, the specular partner sent by
 // (x - c_kx, y, z - c_kz) in the direction with the y component reversed.
 template <int K>
-__device__ __forceinline__ long long recv_index(const Grid3& G, int x, int y, int z, int& kk) {
-    int sy = y - cy3(K);
-    kk = K;
-    if (sy < 0 || sy >= G.ny) {
-        sy = y;
-        kk = miry3(K);
-    }
-    return (long long)(kk - 1) * G.N + G.idx(G.wx(x - cx3(K)), sy, G.wz(z - cz3(K)));
+__device__ __forceinline__ long long recv_index(const Grid3& G, const Nbr& nb) {
+    if (nb.out<-cy3(K)>()) return (long long)(miry3(K) - 1) * G.N + nb.at<-cx3(K), 0, -cz3(K)>();
+    return (long long)(K - 1) * G.N + nb.at<-cx3(K), -cy3(K), -cz3(K)>();
 }
 
 template <int I, int E, class F>
@@ -145,6 +173,7 @@ __global__ void __launch_bounds__(T3) moments3d(const Args3 A) {
     const float isc[2] = {1.0f / scl[0], 1.0f / scl[1]};
     const int nsets = A.P.psi_on ? 2 : 1;
     for_cells(G, [&](long long c, int x, int y, int z) {
+        const Nbr nb(G, c, x, y, z);
         for (int s = 0; s < 2; ++s) {
             float2* out = s == 0 ? A.phi : A.psi;
             if (s >= nsets) {
@@ -156,9 +185,7 @@ __global__ void __launch_bounds__(T3) moments3d(const Args3 A) {
             long long diff = 0;
             sfor<1, Q3>([&](auto KI) {
                 constexpr int k = decltype(KI)::value;
-                int kk;
-                const long long src = recv_index<k>(G, x, y, z, kk);
-                diff += (long long)__float2int_rn(__ldg(pop + src) * scl[s]);
+                diff += (long long)__float2int_rn(__ldg(pop + recv_index<k>(G, nb)) * scl[s]);
                 diff -= (long long)__float2int_rn(__ldg(pop + (long long)(k - 1) * G.N + c) * scl[s]);
             });
             // |diff| < 2^31: split into a multiple of 4096 and a remainder, each exact in
@@ -173,19 +200,11 @@ __global__ void __launch_bounds__(T3) moments3d(const Args3 A) {
 // ------------------------------------------------------------------ potentials3d
 // value of a moment field at the neighbour x + c_k, with the ghost value of Eq. boundary
 // (G) or the mirror value (N) beyond a wall
-template <int K, bool GHOST>
-__device__ __forceinline__ void nb_vals(const Args3& A, int x, int y, int z, float& ph, float& ps) {
-    const Grid3& G = A.g;
-    const int ny2 = y + cy3(K);
-    const long long i = G.idx(G.wx(x + cx3(K)), (ny2 < 0 || ny2 >= G.ny) ? y : ny2, G.wz(z + cz3(K)));
+template <int K>
+__device__ __forceinline__ void nb_vals(const Args3& A, const Nbr& nb, float& ph, float& ps) {
+    const long long i = nb.at<cx3(K), cy3(K), cz3(K)>();
     ph = A.phi[i].x;
     ps = A.psi[i].x;
-    if (GHOST && (ny2 < 0 || ny2 >= G.ny)) {
-        float gph, gps;
-        wall_ghost(ph, ps, ny2 < 0 ? 0 : 1, A.P, gph, gps);
-        ph = gph;
-        ps = gps;
-    }
 }
 
 __global__ void __launch_bounds__(T3) potentials3d(const Args3 A, int diag) {
@@ -200,13 +219,21 @@ __global__ void __launch_bounds__(T3) potentials3d(const Args3 A, int diag) {
         const float phi = pc.x, psi = sc.x;
         float lgp = 0.f, lgs = 0.f, lnp = 0.f, lns = 0.f;
         const bool wall = (y == 0 || y == G.ny - 1);
+        const Nbr nb(G, c, x, y, z);
         sfor<1, Q3>([&](auto KI) {
             constexpr int k = decltype(KI)::value;
             float ph, ps;
-            nb_vals<k, false>(A, x, y, z, ph, ps);
+            nb_vals<k>(A, nb, ph, ps);
             lnp += w3(k) * ph;
             lns += w3(k) * ps;
-            if (wall) nb_vals<k, true>(A, x, y, z, ph, ps);
+            if (wall && nb.out<cy3(k)>()) {
+                // beyond a wall: the mirror value for the Neumann Laplacian, the ghost value of
+                // Eq. boundary (from the wall-row values at x + c) for the wetting one
+                float gph, gps;
+                wall_ghost(ph, ps, cy3(k) < 0 ? 0 : 1, A.P, gph, gps);
+                ph = gph;
+                ps = gps;
+            }
             lgp += w3(k) * ph;
             lgs += w3(k) * ps;
         });
@@ -284,24 +311,23 @@ __global__ void __launch_bounds__(T3, 2) collide3d(const Args3 A) {
         const float2 pcf = A.phi[c], scf = A.psi[c];
         const float phi = pcf.x, psi = scf.x;
         // flow pull with halfway bounce-back (moving wall along x)
+        const Nbr nb(G, c, x, y, z);
         float f[Q3];
         sfor<0, Q3>([&](auto KI) {
             constexpr int k = decltype(KI)::value;
-            const int sy = y - cy3(k);
-            if (sy < 0 || sy >= G.ny) {
+            if (nb.out<-cy3(k)>()) {
                 constexpr int o = opp3(k);
-                const float uw = P.uw[sy < 0 ? 0 : 1];
+                const float uw = P.uw[cy3(k) > 0 ? 0 : 1];
                 f[k] = __ldg(A.f_in + (long long)o * N + c) - 6.0f * w3(o) * rho * (float)cx3(o) * uw;
             } else {
-                f[k] = __ldg(A.f_in + (long long)k * N + G.idx(G.wx(x - cx3(k)), sy, G.wz(z - cz3(k))));
+                f[k] = __ldg(A.f_in + (long long)k * N + nb.at<-cx3(k), -cy3(k), -cz3(k)>());
             }
         });
         // gradients of the potentials (mirror values beyond a wall)
         float gmx = 0.f, gmy = 0.f, gmz = 0.f, gpx = 0.f, gpy = 0.f, gpz = 0.f;
         sfor<1, Q3>([&](auto KI) {
             constexpr int k = decltype(KI)::value;
-            const int ny2 = y + cy3(k);
-            const long long i = G.idx(G.wx(x + cx3(k)), (ny2 < 0 || ny2 >= G.ny) ? y : ny2, G.wz(z + cz3(k)));
+            const long long i = nb.at<cx3(k), cy3(k), cz3(k)>();   // mirror value beyond a wall
             const float mu = 3.0f * w3(k) * __ldg(A.mu_phi + i), mp = 3.0f * w3(k) * __ldg(A.mu_psi + i);
             if constexpr (cx3(k) != 0) { gmx += cx3(k) * mu; gpx += cx3(k) * mp; }
             if constexpr (cy3(k) != 0) { gmy += cy3(k) * mu; gpy += cy3(k) * mp; }
@@ -395,8 +421,7 @@ __global__ void __launch_bounds__(T3, 2) collide3d(const Args3 A) {
             const float dRf = dR.hi + dR.lo;
             sfor<1, Q3>([&](auto KI) {
                 constexpr int k = decltype(KI)::value;
-                int kk;
-                const float gk = __ldg(pop + recv_index<k>(G, x, y, z, kk));
+                const float gk = __ldg(pop + recv_index<k>(G, nb));
                 const float geq = w3(k) * (eta * cval + cdot3<k>(cux, cuy, cuz));
                 pout[(long long)(k - 1) * N + c] = gk + sr * (geq - gk) + a * w3(k) * cdot3<k>(ax, ay, az) + w3(k) * dRf;
             });
