@@ -1,0 +1,63 @@
+"""Spurious currents of a static surfactant-laden drop at the paper's density and viscosity
+ratios (Sec. 4.2, Table 2), through the batch kernel.
+
+The paper's case: [0, 1]^2, a circular drop R = 0.25 at the centre, rho_l / rho_g = 1000,
+mu_l / mu_g = 100, rho_g = 1, mu_g = 0.1, sigma = 0.001, eps = 0.025, lambda_s = 0,
+k_B T = 0.162 and W = 0.24 (Pi = 1.35, Ex = 0.5 in units of beta), psi_b in {0.001, 0.005,
+0.01, 0.1}; |u|max at t = 40 decreases with refinement.  Here (readings of the unstated
+scaling and of the geometry): dx = 1 / n and dt = dx^2, which puts the viscosities at
+tau = 0.53 (liquid) and 0.8 (gas); sigma_lattice = sigma dt^2 / dx^3 = 0.001 / n;
+eps = 0.025 n nodes; tau_g = tau_h = 0.8 and M_psi = 0.5 (mobilities unstated in lattice
+form); the box has the solver's neutral no-slip walls at y = 0, 1 (0.25 from the drop) and
+is periodic in x.  Checked at t = 5 on n = 150 and 200 (the currents settle by t ~ 5):
+finite everywhere, |u|max falls by more than 4x from n = 150 to 200 for psi_b <= 0.01
+(measured 5.5-6x) and by more than 2x at psi_b = 0.1 (measured 2.6x), and is smallest at
+psi_b = 0.1, as in the paper's table.  (n = 100, eps = 2.5 nodes, is unstable in this
+scheme at psi_b <= 0.01.)
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+PSIB = (0.001, 0.005, 0.01, 0.1)
+
+
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _umax(n, t):
+    import torch
+    from paper_2609_26332_b300 import binding as B, inputs
+    eps = 0.025 * n
+    params, walls, fields = [], [], []
+    for pb in PSIB:
+        params.append(B.default_params(n, n, eps=eps, sigma=0.001 / n, rho_l=1000.0, rho_g=1.0, tau_f=0.53,
+                                       tau_f_gas=0.8, tau_g=0.8, tau_h=0.8, Ex=0.5, Pi=1.35, lambda_s=0.0,
+                                       psi_b=pb, M_psi=0.5, multiplier=B.TARGET))
+        walls.append(((90.0, 0.0, 0.0, 0.0), (90.0, 0.0, 0.0, 0.0)))
+        fields.append(inputs.free_drop(n, n, 0.25 * n, eps, phi_b=inputs.bulk_phi(pb, 0.5), psi0=pb))
+    st = torch.cuda.Stream()
+    out = []
+    with B.Batch(params, walls, stream=st) as b:
+        for i, (phi, psi) in enumerate(fields):
+            b.init_fields(i, phi, psi)
+        b.set_tiling(64, 2, 64)
+        b.step(int(t * n * n))
+        for i in range(len(PSIB)):
+            f = b.read_fields(i, which=("ux", "uy"))
+            tot = b.read_totals(i)
+            assert tot["range_count"] == 0 and np.isfinite(f["ux"]).all()
+            out.append(float(np.hypot(f["ux"], f["uy"]).max()) * n)   # physical units: dx / dt = n
+    return np.array(out)
+
+
+def test_spurious_currents_fall_under_refinement():
+    _cuda()
+    u150, u200 = _umax(150, 5.0), _umax(200, 5.0)
+    print("physical |u|max at t = 5, psi_b", PSIB, ": n = 150", u150, " n = 200", u200)
+    assert (u200[:3] < u150[:3] / 4).all() and u200[3] < u150[3] / 2
+    assert u150.argmin() == 3 and u200.argmin() == 3
