@@ -347,6 +347,12 @@ slbm_status slbm_load(slbm_domain* d, const char* path);
 /* Bytes of device memory the domain holds. */
 size_t slbm_device_bytes(const slbm_domain* d);
 
+/* Number of device allocations (cudaMalloc calls) the library has made in this process,
+ * for every domain, batch and network together: a caller that must not allocate once
+ * running (domains built with slbm_create_domain_ext, slbm_read_fields_noalloc) can check
+ * that the count does not move across its calls.  Thread-safe. */
+unsigned long long slbm_device_allocations(void);
+
 /* Releases everything the domain owns (NULL is a no-op). */
 void slbm_destroy(slbm_domain* d);
 

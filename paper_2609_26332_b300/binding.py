@@ -79,6 +79,8 @@ def _load():
     L.slbm_read_fields_noalloc.restype = ctypes.c_int
     L.slbm_device_bytes.argtypes = [vp]
     L.slbm_device_bytes.restype = ctypes.c_size_t
+    L.slbm_device_allocations.argtypes = []
+    L.slbm_device_allocations.restype = ctypes.c_ulonglong
     L.slbm_workspace_bytes.argtypes = [ctypes.POINTER(Params)]
     L.slbm_workspace_bytes.restype = ctypes.c_size_t
     L.slbm_create_domain_ext.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
@@ -320,6 +322,11 @@ class Domain:
 
 def version():
     return lib.slbm_version().decode()
+
+
+def device_allocations():
+    """slbm_device_allocations: device allocations the library has made in this process."""
+    return int(lib.slbm_device_allocations())
 
 
 class Domain3D:

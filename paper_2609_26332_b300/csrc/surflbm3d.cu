@@ -544,7 +544,7 @@ slbm_status cuda_fail3(slbm3d_domain* d, cudaError_t e, const char* what) {
 
 template <class P>
 cudaError_t alloc3(slbm3d_domain* d, P** ptr, size_t bytes) {
-    cudaError_t e = cudaMalloc((void**)ptr, bytes);
+    cudaError_t e = slbm_device_malloc((void**)ptr, bytes);
     if (e == cudaSuccess) d->bytes += bytes;
     else *ptr = nullptr;
     return e;

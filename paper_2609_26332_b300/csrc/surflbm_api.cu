@@ -5,6 +5,7 @@
 
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -416,7 +417,7 @@ slbm_status dalloc(slbm_domain* d, P** ptr, size_t bytes) {
         d->bytes += bytes;
         return SLBM_OK;
     }
-    cudaError_t e = cudaMalloc((void**)ptr, bytes);
+    cudaError_t e = slbm_device_malloc((void**)ptr, bytes);
     if (e != cudaSuccess) {
         *ptr = nullptr;
         cudaGetLastError();
@@ -528,6 +529,14 @@ void fill_totals(const slbm_domain* d, const Rec& r, slbm_totals* t) {
 }
 
 }  // namespace
+
+std::atomic<unsigned long long> g_device_allocs{0};
+
+cudaError_t slbm_device_malloc(void** ptr, size_t bytes) {
+    const cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) g_device_allocs.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
 
 // parameter checks and derivation shared with the three-dimensional domain
 std::string slbm_validate_params(const slbm_params* p) { return validate(p); }
@@ -930,6 +939,8 @@ slbm_status slbm_set_mms(slbm_domain* d, const slbm_mms* m) {
 }
 
 size_t slbm_device_bytes(const slbm_domain* d) { return d ? d->bytes : 0; }
+
+unsigned long long slbm_device_allocations(void) { return g_device_allocs.load(std::memory_order_relaxed); }
 
 }  // extern "C"
 

@@ -157,7 +157,7 @@ slbm_status build_tables(slbm_batch* b) {
     b->npieces = (int)pieces.size();
     cudaError_t e = cudaSuccess;
     if (b->npieces > 0) {
-        e = cudaMalloc(&b->d_pieces, pieces.size() * sizeof(Piece));
+        e = slbm_device_malloc((void**)&b->d_pieces, pieces.size() * sizeof(Piece));
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(b->d_pieces, pieces.data(), pieces.size() * sizeof(Piece), cudaMemcpyHostToDevice, b->stream);
     }
@@ -292,7 +292,7 @@ slbm_status residuals(slbm_batch* b, long long K, std::vector<double>& r) {
         cudaFree(b->d_res);
         b->d_res = nullptr;
         b->res_bytes = 0;
-        e = cudaMalloc(&b->d_res, bytes);
+        e = slbm_device_malloc((void**)&b->d_res, bytes);
         if (e != cudaSuccess) return bcuda(b, e, "residual scratch");
         b->res_bytes = bytes;
         b->bytes += bytes;
@@ -410,12 +410,12 @@ slbm_status slbm_create_batch(const slbm_params* params, const slbm_wall_spec* w
         b->snap_off[i] = snap_total;
         snap_total += 2 * (size_t)d->N;
     }
-    cudaError_t e = cudaMalloc(&b->d_inst, count * sizeof(InstDesc));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_partials, part_total * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, count * sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, 2 * sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_G, sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_snap_base, snap_total * sizeof(float));
+    cudaError_t e = slbm_device_malloc((void**)&b->d_inst, count * sizeof(InstDesc));
+    if (e == cudaSuccess) e = slbm_device_malloc((void**)&b->d_partials, part_total * sizeof(double));
+    if (e == cudaSuccess) e = slbm_device_malloc((void**)&b->d_counters, count * sizeof(unsigned int));
+    if (e == cudaSuccess) e = slbm_device_malloc((void**)&b->d_queue, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = slbm_device_malloc((void**)&b->d_G, sizeof(long long));
+    if (e == cudaSuccess) e = slbm_device_malloc((void**)&b->d_snap_base, snap_total * sizeof(float));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, count * sizeof(unsigned int), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(unsigned int), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_G, 0, sizeof(long long), b->stream);

@@ -43,6 +43,10 @@ struct slbm_domain {
     std::string err = "no error";
 };
 
+// cudaMalloc counted in the process-wide total that slbm_device_allocations reports; every
+// device allocation of the library goes through it.
+cudaError_t slbm_device_malloc(void** ptr, size_t bytes);
+
 // Parameter checks (empty string: valid), derivation of the model constants and Phys, and
 // one wall's Phys entries (surflbm_api.cu); also used by the three-dimensional domain.
 std::string slbm_validate_params(const slbm_params* p);

@@ -712,7 +712,7 @@ template <class T>
 cudaError_t walloc(slbm_ws* n, T** p, size_t count) {
     void* q = nullptr;
     const size_t b = count * sizeof(T);
-    cudaError_t e = cudaMalloc(&q, b ? b : 16);
+    cudaError_t e = slbm_device_malloc((void**)&q, b ? b : 16);
     if (e == cudaSuccess) {
         n->allocs.push_back(q);
         n->bytes += b;
