@@ -1,7 +1,7 @@
-"""D3Q19 lattice constants of the oracle's three-dimensional extension (TEST INFRASTRUCTURE
-ONLY, see ``oracle/__init__``) (Sec. 2.3
-states the model for d = 2, 3; Sec. 3 writes the lattice Boltzmann scheme for a DdQq
-lattice).
+"""D3Q19 lattice constants of the oracle's three-dimensional extension.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).  Sec. 2.3 states the model for d = 2, 3;
+Sec. 3 writes the lattice Boltzmann scheme for a DdQq lattice.
 
 Velocity ordering: rest, the six axis links (+x, -x, +y, -y, +z, -z), then the twelve
 edge diagonals in the xy, xz and yz planes.  Weights 1/3, 1/18, 1/36; c_s^2 = 1/3.
