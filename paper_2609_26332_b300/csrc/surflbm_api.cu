@@ -199,7 +199,7 @@ StepArgs<T> make_args(slbm_domain* d, bool diag) {
     StepArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     const int i = d->cur, o = d->cur ^ 1;
-    a.nx = d->p.nx; a.ny = d->p.ny; a.N = d->N; a.total = d->total;
+    a.nx = d->p.nx; a.ny = d->p.ny; a.N = d->N; a.total = d->total; a.band_h = d->band_h;
     a.f_in = (const T*)d->f[i]; a.gd_in = (const T*)d->gd[i]; a.gm_in = d->gm[i];
     a.hd_in = (const T*)d->hd[i]; a.hm_in = d->hm[i]; a.php_in = d->php[i];
     a.f_out = (T*)d->f[o]; a.gd_out = (T*)d->gd[o]; a.gm_out = d->gm[o];
@@ -311,6 +311,49 @@ int choose_ctas(slbm_domain* d, int ctas_per_sm) {
     if (n > slots) n = slots;
     if (n < 1) n = 1;
     return (int)n;
+}
+
+// Band-major split.  The strip-major ranges of choose_ctas balance the rows to within one,
+// but the CTAs of neighbouring strips march different rows at any moment, so the halo
+// columns a strip stages (whole DRAM bursts that the neighbouring strip also reads) are
+// fetched from DRAM twice.  Pieces (band of H rows, strip) taken round-robin, band by band,
+// put the CTAs of neighbouring strips on the same rows at the same time, and the second
+// read of a halo burst hits L2 (measured at 4096 x 2048: 1.25 instead of 1.97 GB read per
+// step).  Chosen when its cost, in rows per CTA plus a prologue per piece, is within
+// BAND_SLACK of the strip-major cost; H at least 16 rows.
+constexpr double BAND_SLACK = 1.05;
+constexpr int PROLOGUE_ROWS = 2;
+void choose_bands(slbm_domain* d, int ctas_per_sm) {
+    d->band_h = 0;
+    const int ny = d->p.ny;
+    const int strips = (int)(d->total / ny);
+    if (strips < 2 || ny < 32) return;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long slots = (long long)sms * ctas_per_sm;
+    const long long g0 = d->grid.x;
+    // strip-major: a CTA marches ceil(total / grid) rows in at most two pieces
+    const double cost_s = (double)((d->total + g0 - 1) / g0) + 2 * PROLOGUE_ROWS;
+    double best = 0.0;
+    int best_h = 0;
+    long long best_g = 0;
+    for (int nb = 2; nb <= ny / 16; ++nb) {
+        const int H = (ny + nb - 1) / nb;
+        const long long pieces = (long long)((ny + H - 1) / H) * strips;
+        const long long g = pieces < slots ? pieces : slots;
+        const long long rounds = (pieces + g - 1) / g;
+        const double cost = (double)rounds * (H + PROLOGUE_ROWS);
+        if (best_h == 0 || cost < best) {
+            best = cost;
+            best_h = H;
+            best_g = g;
+        }
+    }
+    if (best_h > 0 && best <= BAND_SLACK * cost_s) {
+        d->band_h = best_h;
+        d->grid = dim3((unsigned)best_g);
+    }
 }
 
 // ---- tensor maps of the TMA staging (driver entry point looked up once, no libcuda link)
@@ -439,6 +482,7 @@ void plan_domain(slbm_domain* d) {
     }
     d->total = (long long)((p->nx + TX - 1) / TX) * p->ny;
     d->grid = dim3((unsigned)choose_ctas(d, per_sm));
+    choose_bands(d, per_sm);
     if (p->multiplier == SLBM_MULT_EXACT) d->exact_blocks = exact_multiplier_blocks(p->precision, d->N);
 }
 

@@ -16,6 +16,7 @@ struct slbm_domain {
     dim3 grid;
     int exact_blocks = 0;   // grid of the exact-multiplier pass (EXACT mode only)
     long long total = 0;   // strips * ny, the rows the CTAs share out
+    int band_h = 0;        // > 0: band-major split into pieces of band_h rows
     int cur = 0;
     long long n = 0;
     bool initialised = false;

@@ -76,6 +76,7 @@ struct StepArgs {
     int nx, ny;
     long long N;
     long long total;              // strips * ny: the strip-major rows shared out among the CTAs
+    int band_h;                   // > 0: band-major pieces of band_h rows (see the split below)
     // state in (post-collision of the previous step) and out
     const T* f_in; const T* gd_in; const float2* gm_in; const T* hd_in; const float2* hm_in; const float* php_in;
     T* f_out; T* gd_out; float2* gm_out; T* hd_out; float2* hm_out; float* php_out;
