@@ -141,27 +141,41 @@ __device__ __forceinline__ void sfor(F&& f) {
     }
 }
 
-// Every cell once: block b takes a contiguous range of row segments (a segment is up to T3
-// consecutive x of one row (y, z); segment-major order), fixed and deterministic, and steps
-// through it incrementing y and z, so no integer division is done per cell.
+// Every cell once: the row segments (a segment is up to T3 consecutive x of one row
+// (y, z); segment-major order) are dealt round-robin, item blockIdx.x + j gridDim.x to
+// block blockIdx.x, so that at any moment the blocks work on consecutive rows: the
+// neighbours a cell gathers in the planes z - 1 and z + 1 (ny rows away) are read within
+// a few hundred rows of each other, while they are still in L2 (a contiguous range per
+// block put them a block's range apart in time, and the links along z were fetched from
+// DRAM twice).  The block steps through its items incrementing y and z, so no integer
+// division is done per cell.
 template <class F>
 __device__ __forceinline__ void for_cells(const Grid3& G, F&& body) {
     const int nseg = (G.nx + T3 - 1) / T3;
     const int rows = G.ny * G.nz;
     const long long items = (long long)rows * nseg;
-    const long long lo = items * blockIdx.x / gridDim.x, hi = items * (blockIdx.x + 1) / gridDim.x;
-    if (lo >= hi) return;
+    const long long g = gridDim.x;
+    const long long lo = blockIdx.x;
+    if (lo >= items) return;
     int seg = (int)(lo / rows), row = (int)(lo - (long long)seg * rows);
     int y = row % G.ny, z = row / G.ny;
-    for (long long it = lo; it < hi; ++it) {
+    const int dseg = (int)(g / rows), drow = (int)(g - (long long)dseg * rows);
+    const int dy = drow % G.ny, dz = drow / G.ny;
+    for (long long it = lo; it < items; it += g) {
         const int x = seg * T3 + (int)threadIdx.x;
         if (x < G.nx) body((long long)row * G.nx + x, x, y, z);
-        if (++row == rows) {
-            row = y = z = 0;
-            ++seg;
-        } else if (++y == G.ny) {
-            y = 0;
+        seg += dseg;
+        row += drow;
+        y += dy;
+        z += dz;
+        if (y >= G.ny) {
+            y -= G.ny;
             ++z;
+        }
+        if (row >= rows) {
+            row -= rows;
+            z -= G.nz;
+            ++seg;
         }
     }
 }
