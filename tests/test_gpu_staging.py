@@ -1,13 +1,15 @@
 """The two input stagings of the step kernel (slbm_params.staging): TMA tile copies with
-mbarriers against thread-issued cp.async.  They move the same values, so after a few steps
-every field and total is bit-identical, in every storage mode, with the exact multiplier,
-at the periodic seam and across several strips (one wrong staged value would show in the
-first step).  The two are separate kernel instantiations, and the compiler chooses for
-each where plain FP32 expressions become fused multiply-adds, so a rare one-rounding
-difference can appear later and grow: over 300 steps they are compared within rounding
-tolerances (measured: FP32 fields identical, free energy 1e-9 relative; FP16 fields 6e-5
-after a one-rounding difference of the surfactant multiplier near step 20).  The TMA path
-is also checked against the oracle."""
+mbarriers against thread-issued cp.async, in every storage mode, with the exact
+multiplier, at the periodic seam and across several strips.  They move the same values,
+but they are separate kernel instantiations (and the FP32 cp.async one loads the
+collide's inputs earlier), and the compiler chooses for each where plain FP32 expressions
+become fused multiply-adds: the fields agree to rounding, not bitwise.  A wrong staged
+value (a halo column, a seam image, a stale row) changes phi and psi by 1e-2 or more
+within a few steps; after 3 steps the fields are compared to 5e-7 (FP32) and 1e-3 (16-bit
+storage, a few units in the last place of a population), after 300 steps to 1e-5 and
+1e-3 (measured: FP32 at most a few 1e-8; FP16 6e-5 after a one-rounding difference of the
+surfactant multiplier near step 20).  The TMA path is also checked against the oracle.
+"""
 import numpy as np
 import pytest
 
@@ -37,13 +39,12 @@ def test_tma_and_cpasync_staging_agree(precision, multiplier):
                   multiplier=multiplier)
     fa, ta = _run(c, precision, 0, 3)
     fb, tb = _run(c, precision, 1, 3)
+    tol = 5e-7 if precision == "fp32" else 1e-3
     for k in fa:
-        assert np.array_equal(fa[k], fb[k]), k
-    for k in ("psi_total", "H", "lambda_phi"):
-        assert ta[k] == tb[k], k
-    # reduced by the diagnostic pass, itself two instantiations
-    for k in ("free_energy", "kinetic"):
-        assert abs(ta[k] - tb[k]) <= 1e-8 * abs(ta[k]), k
+        assert np.abs(fa[k] - fb[k]).max() <= tol, k
+    assert abs(ta["psi_total"] - tb["psi_total"]) <= 1e-12 * ta["psi_total"]
+    for k, rel in (("H", 1e-6), ("free_energy", 1e-6), ("kinetic", 1e-5)):
+        assert abs(ta[k] - tb[k]) <= rel * abs(ta[k]), k
     fa, ta = _run(c, precision, 0, 300)
     fb, tb = _run(c, precision, 1, 300)
     tol = 1e-5 if precision == "fp32" else 1e-3
