@@ -96,6 +96,8 @@ template <> struct Stor<float> {
     static constexpr float kScale = 1.0f, kInv = 1.0f;
     static __device__ __forceinline__ float ld(const float* p, long long i) { return __ldg(p + i); }
     static __device__ __forceinline__ float lds(const float* p, int i) { return p[i]; }
+    // the stored number without the storage scale (times kInv gives the value)
+    static __device__ __forceinline__ float lds_raw(const float* p, int i) { return p[i]; }
     static __device__ __forceinline__ float rnd(float v) { return v; }
     static __device__ __forceinline__ void st(float* p, long long i, float v) { p[i] = v; }
 };
@@ -106,6 +108,7 @@ template <> struct Stor<__half> {
         return __half2float(__ldg(p + i)) * kInv;
     }
     static __device__ __forceinline__ float lds(const __half* p, int i) { return __half2float(p[i]) * kInv; }
+    static __device__ __forceinline__ float lds_raw(const __half* p, int i) { return __half2float(p[i]); }
     static __device__ __forceinline__ float rnd(float v) { return __half2float(__float2half_rn(v * kScale)) * kInv; }
     static __device__ __forceinline__ void st(__half* p, long long i, float v) { p[i] = __float2half_rn(v * kScale); }
 };
@@ -115,6 +118,7 @@ template <> struct Stor<__nv_bfloat16> {
         return __bfloat162float(__ldg(p + i));
     }
     static __device__ __forceinline__ float lds(const __nv_bfloat16* p, int i) { return __bfloat162float(p[i]); }
+    static __device__ __forceinline__ float lds_raw(const __nv_bfloat16* p, int i) { return __bfloat162float(p[i]); }
     static __device__ __forceinline__ float rnd(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, long long i, float v) { p[i] = __float2bfloat16_rn(v); }
 };
