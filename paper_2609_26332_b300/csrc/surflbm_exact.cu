@@ -51,30 +51,51 @@ __global__ void __launch_bounds__(EX_THREADS) exact_multiplier_kernel(const Exac
     ff acc[NPART];
 #pragma unroll
     for (int q = 0; q < NPART; ++q) acc[q] = {0.0f, 0.0f};
-    // tiles of EX_TX x EX_TY cells, one warp per tile row: the rows y +- 1 a cell gathers
-    // from are mostly the same CTA's rows, still in L1 (N <= 2^28: 32-bit indices)
+    // tiles of EX_TX x EX_TY cells with a one-node halo: each node's eight sent fixed-point
+    // values, h'(phi^n) and zeroth moment are evaluated once into shared memory (phase 1),
+    // then every cell sums what it sends and receives from there (phase 2)
+    constexpr int HX = EX_TX + 2, HN = HX * (EX_TY + 2);
+    __shared__ int sKs[8][HN];
+    __shared__ float sHp[HN];
+    __shared__ float2 sM[HN];
     const int ntx = (a.nx + EX_TX - 1) / EX_TX, nty = (a.ny + EX_TY - 1) / EX_TY;
     const int tx = threadIdx.x % EX_TX, ty = threadIdx.x / EX_TX;
     for (int t = blockIdx.x; t < ntx * nty; t += gridDim.x) {
         const int ty0 = t / ntx;
-        const int x = (t - ty0 * ntx) * EX_TX + tx, y = ty0 * EX_TY + ty;
+        const int x0 = (t - ty0 * ntx) * EX_TX, y0 = ty0 * EX_TY;
+        __syncthreads();   // the previous tile's phase 2 has read the shared arrays
+        for (int q = threadIdx.x; q < HN; q += EX_THREADS) {
+            const int hy = q / HX, hx = q - hy * HX;
+            const int gy = y0 - 1 + hy;
+            if (gy < 0 || gy >= a.ny) continue;   // beyond a wall: the links use mirrors in the own row
+            int gx = (x0 - 1 + hx) % a.nx;
+            if (gx < 0) gx += a.nx;
+            const long long sidx = (long long)gy * a.nx + gx;
+            const float2 m = a.gm[sidx];
+            sM[q] = m;
+#pragma unroll
+            for (int k = 1; k < 9; ++k) sKs[k - 1][q] = sent_fixed(a, sidx, k, m, scl);
+            sHp[q] = P.linear ? 1.0f : hprime(a.php[sidx], P);
+        }
+        __syncthreads();
+        const int x = x0 + tx, y = y0 + ty;
         if (x >= a.nx || y >= a.ny) continue;
-        const long long c = (long long)y * a.nx + x;
-        const float2 m = a.gm[c];
+        const int q0 = (ty + 1) * HX + (tx + 1);
+        const float2 m = sM[q0];
         int ksum = 0;
 #pragma unroll
-        for (int k = 1; k < 9; ++k) ksum += sent_fixed(a, c, k, m, scl);
+        for (int k = 1; k < 9; ++k) ksum += sKs[k - 1][q0];
         int krecv = 0;
         // h' = 1 for the linear constraint: the term's total is exactly N a M_phi lambda
         // (the fixed-point exchange telescopes), so its distribution need not be summed
-        float bsum = P.linear ? 1.0f : Wk(0) * hprime(a.php[c], P);
+        float bsum = P.linear ? 1.0f : Wk(0) * sHp[q0];
 #pragma unroll
         for (int k = 1; k < 9; ++k) {
-            int sy = y - CYk(k), kk = k;
-            if (sy < 0 || sy >= a.ny) { sy = y; kk = MIRYk(k); }
-            const long long s = (long long)sy * a.nx + wrap1(x - CXk(k), a.nx);
-            krecv += sent_fixed(a, s, kk, a.gm[s], scl);
-            if (!P.linear) bsum = __fmaf_rn(Wk(k), hprime(a.php[s], P), bsum);
+            const int sy = y - CYk(k);
+            const bool out = sy < 0 || sy >= a.ny;   // specular: the mirrored direction of the own row
+            const int qs = (ty + 1 - (out ? 0 : CYk(k))) * HX + (tx + 1 - CXk(k));
+            krecv += sKs[(out ? MIRYk(k) : k) - 1][qs];
+            if (!P.linear) bsum = __fmaf_rn(Wk(k), sHp[qs], bsum);
         }
         const ff A = ff_add(ff_add({m.x, m.y}, fixed_to_ff(-ksum, isc)), fixed_to_ff(krecv, isc));
         const float B = coef * bsum;
