@@ -5,14 +5,15 @@
 // moving-wall term for f, specular reflection for g and h, the wall flux in R).
 //
 // State (FP32, SoA planes of N = nx ny nz cells, ping-pong): f* (19 planes), g*_k and h*_k
-// for the 18 moving directions, the zeroth moments m* of g and h as float-float (the rest
-// population is m* minus the moving ones), and the history R^{n-1}, (phi u)^{n-1},
+// for the 18 moving directions, the zeroth moments m* of g and h minus the fixed-point
+// values each node sends (m~, float-float; the rest population is m* minus the moving
+// ones), and the history R^{n-1}, (phi u)^{n-1},
 // (psi u)^{n-1} (8 planes).  One step is three launches:
-//   moments3d     phi, psi = m* - (sent) + (received): every streamed population is
-//                 converted once to 32-bit fixed point by a deterministic rule, so the
-//                 sender's and the receiver's integer agree and the exchange telescopes
-//                 exactly (sum psi, and sum phi under the linear constraint, conserved to
-//                 float-float rounding);
+//   moments3d     phi, psi = m~ + (received), m~ = m* - (sent) stored by the collide: every
+//                 streamed population is converted to 32-bit fixed point by one
+//                 deterministic rule, at the sender (into m~) and at the receiver, so the
+//                 two integers agree and the exchange telescopes exactly (sum psi, and sum
+//                 phi under the linear constraint, conserved to float-float rounding);
 //   potentials3d  mu_phi, mu_psi (Eqs. eq_muphi, eq_mupsi) with the isotropic D3Q19
 //                 Laplacian and the ghost planes, the free reaction terms, and the FP64
 //                 integrals; the last block resolves lambda_phi (Eq. eq15) and mubar_psi
@@ -141,6 +142,15 @@ __device__ __forceinline__ void sfor(F&& f) {
     }
 }
 
+// exact float-float value of an int64 fixed-point number K * isc (|K| < 2^43, isc a power
+// of two): the high part (|K >> 24| < 2^19) and the low 24 bits are each exact in FP32
+__device__ __forceinline__ ff fixed64_to_ff(long long K, float isc) {
+    const long long kh = K >> 24;
+    const float hi = __fmul_rn((float)kh, __fmul_rn(16777216.0f, isc));
+    const float lo = __fmul_rn((float)(K - (kh << 24)), isc);
+    return two_sum(hi, lo);
+}
+
 // Every cell once: the row segments (a segment is up to T3 consecutive x of one row
 // (y, z); segment-major order) are dealt round-robin, item blockIdx.x + j gridDim.x to
 // block blockIdx.x, so that at any moment the blocks work on consecutive rows: the
@@ -195,17 +205,15 @@ __global__ void __launch_bounds__(T3) moments3d(const Args3 A) {
                 continue;
             }
             const float* pop = s == 0 ? A.g_in : A.h_in;
+            // the stored moment is m~ = m* minus everything the node sent (the collide, or
+            // the initialisation, subtracted it), so phi = m~ + (everything received)
             const float2 m = (s == 0 ? A.gm_in : A.hm_in)[c];
-            long long diff = 0;
+            long long kr = 0;
             sfor<1, Q3>([&](auto KI) {
                 constexpr int k = decltype(KI)::value;
-                diff += (long long)__float2int_rn(__ldg(pop + recv_index<k>(G, nb)) * scl[s]);
-                diff -= (long long)__float2int_rn(__ldg(pop + (long long)(k - 1) * G.N + c) * scl[s]);
+                kr += (long long)__float2int_rn(__fmul_rn(__ldg(pop + recv_index<k>(G, nb)), scl[s]));
             });
-            // |diff| < 2^31: split into a multiple of 4096 and a remainder, each exact in
-            // float-float (fixed_to_ff keeps at most 20 significant bits per float)
-            const int dh = (int)(diff / 4096) * 4096;
-            const ff v = ff_add(ff_add({m.x, m.y}, fixed_to_ff(dh, isc[s])), fixed_to_ff((int)(diff - dh), isc[s]));
+            const ff v = ff_add({m.x, m.y}, fixed64_to_ff(kr, isc[s]));
             out[c] = make_float2(v.hi, v.lo);
         }
     });
@@ -433,13 +441,19 @@ __global__ void __launch_bounds__(T3, 2) collide3d(const Args3 A) {
             const float ax = 3.0f * d[3 * s], ay = 3.0f * d[3 * s + 1], az = 3.0f * d[3 * s + 2];
             const float a = 1.0f - 0.5f * sr;
             const float dRf = dR.hi + dR.lo;
+            const float scl = s == 0 ? (float)(1u << SFIX_PHI) : 2147483648.0f;
+            long long ks = 0;   // the fixed-point values this node sends (the rule of moments3d)
             sfor<1, Q3>([&](auto KI) {
                 constexpr int k = decltype(KI)::value;
                 const float gk = __ldg(pop + recv_index<k>(G, nb));
                 const float geq = w3(k) * (eta * cval + cdot3<k>(cux, cuy, cuz));
-                pout[(long long)(k - 1) * N + c] = gk + sr * (geq - gk) + a * w3(k) * cdot3<k>(ax, ay, az) + w3(k) * dRf;
+                const float v = gk + sr * (geq - gk) + a * w3(k) * cdot3<k>(ax, ay, az) + w3(k) * dRf;
+                pout[(long long)(k - 1) * N + c] = v;
+                ks += (long long)__float2int_rn(__fmul_rn(v, scl));
             });
-            const ff ms = ff_add(cff, dR);
+            // stored: m~ = m* minus everything sent, so the next moments pass adds only what
+            // each node receives and the exchange still telescopes exactly
+            const ff ms = ff_add(ff_add(cff, dR), fixed64_to_ff(-ks, 1.0f / scl));
             (s == 0 ? A.gm_out : A.hm_out)[c] = make_float2(ms.hi, ms.lo);
             hs[(long long)s * N] = Rstore;
             hs[(long long)(2 + 3 * s) * N] = s == 0 ? phux : psux;
@@ -493,6 +507,8 @@ __global__ void init3d(Grid3 G, const double* phi0, const double* psi0, int psi_
         const double eta = s == 0 ? eta_phi : eta_psi;
         float* pop = s == 0 ? g : h;
         double msum = on ? (1.0 - (1.0 - w3d(0)) * eta) * F[c] : 0.0;
+        const float scl = s == 0 ? (float)(1u << SFIX_PHI) : 2147483648.0f;
+        long long ks = 0;
         for (int k = 1; k < Q3; ++k) {
             int ty = y + cy3(k);
             if (ty < 0 || ty >= G.ny) ty = y;
@@ -502,10 +518,13 @@ __global__ void init3d(Grid3 G, const double* phi0, const double* psi0, int psi_
             // the exact value: every initial value is sent exactly once, so the grid total
             // of the zeroth moments (and of phi, psi after the first pull) is that of F
             msum += v;
+            ks += (long long)__float2int_rn(__fmul_rn((float)v, scl));
         }
-        // the rest population w_0 eta F plus (1 - eta) F is part of the zeroth moment
-        const float hi = (float)msum;
-        (s == 0 ? gm : hm)[c] = make_float2(hi, (float)(msum - (double)hi));
+        // the rest population w_0 eta F plus (1 - eta) F is part of the zeroth moment; stored
+        // minus the fixed-point values the node sends (m~, as the collide stores it)
+        const double mt = msum - (double)ks / (double)scl;
+        const float hi = (float)mt;
+        (s == 0 ? gm : hm)[c] = make_float2(hi, (float)(mt - (double)hi));
     }
     for (int k = 0; k < Q3; ++k) {
         const int ty = y + cy3(k);
