@@ -9,7 +9,7 @@
  * near-equilibrium (phi, psi) field, which is projected onto the conserved totals of the
  * cold start (sum psi of Eq. AC_psi's constraint, H = sum h_phi(phi) of Eq. conservation)
  * and used as the initial state; the lattice Boltzmann relaxation then finishes the job
- * and judges the prediction.
+ * and its step count measures the prediction.
  *
  * Network (fixed architecture, ny and nx divisible by 8):
  *   input 16 channels: the 5 normalised parameters and 11 fixed coordinate features
