@@ -128,9 +128,10 @@ struct Args3 {
 // The population node (x, y, z) receives in direction k: the one sent by x - c_k, or, for
 // a link whose source lies beyond a y-wall, the specular partner sent by
 // (x - c_kx, y, z - c_kz) in the direction with the y component reversed.
-template <int K>
+// IN (compile time): the node's row is off both walls, no link leaves the channel
+template <int K, bool IN = false>
 __device__ __forceinline__ long long recv_index(const Grid3& G, const Nbr& nb) {
-    if (nb.out<-cy3(K)>()) return (long long)(miry3(K) - 1) * G.N + nb.at<-cx3(K), 0, -cz3(K)>();
+    if (!IN && nb.out<-cy3(K)>()) return (long long)(miry3(K) - 1) * G.N + nb.at<-cx3(K), 0, -cz3(K)>();
     return (long long)(K - 1) * G.N + nb.at<-cx3(K), -cy3(K), -cz3(K)>();
 }
 
@@ -196,7 +197,9 @@ __global__ void __launch_bounds__(T3) moments3d(const Args3 A) {
     const float scl[2] = {(float)(1u << SFIX_PHI), 2147483648.0f};
     const float isc[2] = {1.0f / scl[0], 1.0f / scl[1]};
     const int nsets = A.P.psi_on ? 2 : 1;
-    for_cells(G, [&](long long c, int x, int y, int z) {
+    // rows off the walls take a variant without the wall tests of the links
+    auto cell = [&](auto in_c, long long c, int x, int y, int z) {
+        constexpr bool IN = decltype(in_c)::value;
         const Nbr nb(G, c, x, y, z);
         for (int s = 0; s < 2; ++s) {
             float2* out = s == 0 ? A.phi : A.psi;
@@ -211,11 +214,15 @@ __global__ void __launch_bounds__(T3) moments3d(const Args3 A) {
             long long kr = 0;
             sfor<1, Q3>([&](auto KI) {
                 constexpr int k = decltype(KI)::value;
-                kr += (long long)__float2int_rn(__fmul_rn(__ldg(pop + recv_index<k>(G, nb)), scl[s]));
+                kr += (long long)__float2int_rn(__fmul_rn(__ldg(pop + recv_index<k, IN>(G, nb)), scl[s]));
             });
             const ff v = ff_add({m.x, m.y}, fixed64_to_ff(kr, isc[s]));
             out[c] = make_float2(v.hi, v.lo);
         }
+    };
+    for_cells(G, [&](long long c, int x, int y, int z) {
+        if (y > 0 && y < G.ny - 1) cell(std::true_type{}, c, x, y, z);
+        else cell(std::false_type{}, c, x, y, z);
     });
 }
 
@@ -329,7 +336,9 @@ __global__ void __launch_bounds__(T3, 2) collide3d(const Args3 A) {
     const ff uphi = uniform_part(P.M_phi_d * rn.lam, P.M_phi_d * rp.lam, A.first);
     float kin = 0.f;
     int range = 0;
-    for_cells(G, [&](long long c, int x, int y, int z) {
+    // rows off the walls take a variant without the wall tests of the links
+    auto cell = [&](auto in_c, long long c, int x, int y, int z) {
+        constexpr bool IN = decltype(in_c)::value;
         const float2 pcf = A.phi[c], scf = A.psi[c];
         const float phi = pcf.x, psi = scf.x;
         // flow pull with halfway bounce-back (moving wall along x)
@@ -337,7 +346,7 @@ __global__ void __launch_bounds__(T3, 2) collide3d(const Args3 A) {
         float f[Q3];
         sfor<0, Q3>([&](auto KI) {
             constexpr int k = decltype(KI)::value;
-            if (nb.out<-cy3(k)>()) {
+            if (!IN && nb.out<-cy3(k)>()) {
                 constexpr int o = opp3(k);
                 const float uw = P.uw[cy3(k) > 0 ? 0 : 1];
                 f[k] = __ldg(A.f_in + (long long)o * N + c) - 6.0f * w3(o) * rho * (float)cx3(o) * uw;
@@ -445,7 +454,7 @@ __global__ void __launch_bounds__(T3, 2) collide3d(const Args3 A) {
             long long ks = 0;   // the fixed-point values this node sends (the rule of moments3d)
             sfor<1, Q3>([&](auto KI) {
                 constexpr int k = decltype(KI)::value;
-                const float gk = __ldg(pop + recv_index<k>(G, nb));
+                const float gk = __ldg(pop + recv_index<k, IN>(G, nb));
                 const float geq = w3(k) * (eta * cval + cdot3<k>(cux, cuy, cuz));
                 const float v = gk + sr * (geq - gk) + a * w3(k) * cdot3<k>(ax, ay, az) + w3(k) * dRf;
                 pout[(long long)(k - 1) * N + c] = v;
@@ -460,6 +469,10 @@ __global__ void __launch_bounds__(T3, 2) collide3d(const Args3 A) {
             hs[(long long)(3 + 3 * s) * N] = s == 0 ? phuy : psuy;
             hs[(long long)(4 + 3 * s) * N] = s == 0 ? phuz : psuz;
         }
+    };
+    for_cells(G, [&](long long c, int x, int y, int z) {
+        if (y > 0 && y < G.ny - 1) cell(std::true_type{}, c, x, y, z);
+        else cell(std::false_type{}, c, x, y, z);
     });
     if constexpr (DIAG) {
         // kinetic energy and the range flag of the diagnostic level into its record
