@@ -336,9 +336,11 @@ __global__ void __launch_bounds__(T3, 2) collide3d(const Args3 A) {
     const ff uphi = uniform_part(P.M_phi_d * rn.lam, P.M_phi_d * rp.lam, A.first);
     float kin = 0.f;
     int range = 0;
-    // rows off the walls take a variant without the wall tests of the links
-    auto cell = [&](auto in_c, long long c, int x, int y, int z) {
+    // the common case takes a compile-time variant: the row off both walls (no wall tests
+    // of the links), and FAST: the surfactant on, the paper's multiplier, not the first step
+    auto cell = [&](auto in_c, auto fast_c, long long c, int x, int y, int z) {
         constexpr bool IN = decltype(in_c)::value;
+        constexpr bool FAST = decltype(fast_c)::value;
         const float2 pcf = A.phi[c], scf = A.psi[c];
         const float phi = pcf.x, psi = scf.x;
         // flow pull with halfway bounce-back (moving wall along x)
@@ -407,7 +409,7 @@ __global__ void __launch_bounds__(T3, 2) collide3d(const Args3 A) {
         const float phux = phi * ux, phuy = phi * uy, phuz = phi * uz;
         const float psux = psi * ux, psuy = psi * uy, psuz = psi * uz;
         float Rp_phi = 0.f, Rp_psi = 0.f, d[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (!A.first) {
+        if (FAST || !A.first) {
             Rp_phi = hs[0];
             Rp_psi = hs[N];
             d[0] = phux - hs[2 * N]; d[1] = phuy - hs[3 * N]; d[2] = phuz - hs[4 * N];
@@ -415,24 +417,24 @@ __global__ void __launch_bounds__(T3, 2) collide3d(const Args3 A) {
         }
         const float rfp = A.rf_phi[c], rfs = A.rf_psi[c];
         for (int s = 0; s < 2; ++s) {
-            if (s == 1 && !P.psi_on) {
+            if (!FAST && s == 1 && !P.psi_on) {
                 break;
             }
             const ff cff = s == 0 ? ff{pcf.x, pcf.y} : ff{scf.x, scf.y};
             ff dR;
             float Rstore;
-            if (s == 0 && !P.linear) {
+            if (s == 0 && (FAST || !P.linear)) {
                 // R_phi = free part + M_phi lambda^n h'(phi), both in float (sum phi is not a
                 // conserved quantity of the nonlinear constraint)
                 const float R = rfp + lamM * hprime(phi, P);
-                dR = {A.first ? R : 1.5f * R - 0.5f * Rp_phi, 0.f};
+                dR = {(!FAST && A.first) ? R : 1.5f * R - 0.5f * Rp_phi, 0.f};
                 Rstore = R;
             } else {
                 // free part exactly in float-float plus the uniform part, so that the sum
                 // over the grid cancels: 1.5 R^n - 0.5 R^{n-1}
                 const float Rf = s == 0 ? rfp : rfs;
                 const ff un = s == 0 ? uphi : upsi;
-                if (A.first) {
+                if (!FAST && A.first) {
                     dR = ff_add(ff{Rf, 0.f}, un);
                 } else {
                     const ff t = two_sum(Rf, -(s == 0 ? Rp_phi : Rp_psi));
@@ -470,9 +472,14 @@ __global__ void __launch_bounds__(T3, 2) collide3d(const Args3 A) {
             hs[(long long)(4 + 3 * s) * N] = s == 0 ? phuz : psuz;
         }
     };
+    const bool fast = P.psi_on && !P.linear && !A.first;
     for_cells(G, [&](long long c, int x, int y, int z) {
-        if (y > 0 && y < G.ny - 1) cell(std::true_type{}, c, x, y, z);
-        else cell(std::false_type{}, c, x, y, z);
+        if (y > 0 && y < G.ny - 1) {
+            if (fast) cell(std::true_type{}, std::true_type{}, c, x, y, z);
+            else cell(std::true_type{}, std::false_type{}, c, x, y, z);
+        } else {
+            cell(std::false_type{}, std::false_type{}, c, x, y, z);
+        }
     });
     if constexpr (DIAG) {
         // kinetic energy and the range flag of the diagnostic level into its record
