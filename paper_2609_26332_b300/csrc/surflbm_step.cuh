@@ -1,10 +1,12 @@
 // The fused stream-collide kernel of the coupled LBM step and its helpers.
 //
-// Each CTA owns a strip of TX columns and a segment of rows, and marches up the
-// segment RB rows at a time through a software pipeline kept in shared memory rings
-// of 8 rows (row y lives in slot y & 7):
-//   stage K    for every source node of the next rows, the eight populations it sends,
-//              converted once to 32-bit fixed point (both scalar sets);
+// Each CTA owns a strip of TX columns and a segment of rows (pieces of bands of rows,
+// neighbouring strips marched together), and marches up the segment RB rows at a time
+// through a software pipeline kept in shared-memory rings (12 rows for the fixed-point
+// populations and m~, 8 for phi / psi and mu):
+//   stage K    for every source node of the rows seven ahead, the eight populations it
+//              sends, converted once to 32-bit fixed point (both scalar sets), in the same
+//              barrier interval as stage PHI (disjoint rows);
 //   stage PHI  pull: phi, psi of the rows two ahead, exactly, as float-float
 //              (m~ + received - sent, an integer sum that telescopes over the grid);
 //   stage MU   chemical potentials mu_phi, mu_psi (Eqs. eq_muphi, eq_mupsi) one row ahead,
