@@ -266,13 +266,15 @@ slbm_status slbm_batch_init_fields_device(slbm_batch* b, int idx, const double* 
  * columns by default, see slbm_batch_set_strip_width) and bands of about band_rows rows
  * (>= 8), so a piece is a tile of width x band_rows cells and each thread of the CTA
  * marching it (4 rows per step of its pipeline) handles band_rows / 4 cells of it;
- * ctas_per_sm resident CTAs per SM (1 or 2 with 64-column strips, 1 to 3 with 32) take
+ * ctas_per_sm resident CTAs per SM (1 or 2 with 64-column strips, 1 to 3 with 32, 1 with
+ * 128) take
  * pieces from the queue; graph_steps launches per captured graph. */
 slbm_status slbm_batch_set_tiling(slbm_batch* b, int band_rows, int ctas_per_sm, int graph_steps);
 
-/* Strip width of the tile queue: 64 (the step kernel with 256 threads per CTA) or 32 (its
+/* Strip width of the tile queue: 64 (the step kernel with 256 threads per CTA), 32 (its
  * 32-column instance, 128 threads per CTA, more pieces and smaller shared-memory rings for
- * narrow instances at twice the relative halo).  Same method; fields agree to FP32 rounding
+ * narrow instances at twice the relative halo) or 128 (512 threads, one CTA per SM, half
+ * the relative halo for wide instances).  Same method; fields agree to FP32 rounding
  * (the tiling fixes the order of the per-thread partial sums).  Clamps ctas_per_sm to the
  * width's maximum.  EINVAL for other widths. */
 slbm_status slbm_batch_set_strip_width(slbm_batch* b, int width);
@@ -280,7 +282,7 @@ slbm_status slbm_batch_set_strip_width(slbm_batch* b, int width);
 /* The current tiling: strip width, band rows, resident CTAs per SM (any may be NULL). */
 slbm_status slbm_batch_get_tiling(const slbm_batch* b, int* strip_width, int* band_rows, int* ctas_per_sm);
 
-/* Times the candidate tilings (strip width 64 or 32 x band_rows 16..256 x every allowed
+/* Times the candidate tilings (strip width 64, 32 or 128 x band_rows 16..256 x every allowed
  * CTAs-per-SM count) on this batch and keeps the fastest; the choice is read from /
  * appended to the JSON file cache_path (may be NULL) as [band_rows, ctas_per_sm,
  * strip_width], keyed by precision, instance count, total cells and the size list.  The

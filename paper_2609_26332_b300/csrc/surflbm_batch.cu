@@ -6,13 +6,19 @@
 // in a JSON file.
 #include "surflbm_internal.cuh"
 
-// the step kernel with 32-column strips (128 threads per CTA), the batch's second tile shape
+// the step kernel with 32-column strips (128 threads per CTA) and with 128-column strips
+// (512 threads, one CTA per SM), the batch's other tile shapes
 namespace slbm {
 namespace w32 {
 #define SLBM_TILE_TX 32
 #include "surflbm_step_tile.inc"
 #undef SLBM_TILE_TX
 }  // namespace w32
+namespace w128 {
+#define SLBM_TILE_TX 128
+#include "surflbm_step_tile.inc"
+#undef SLBM_TILE_TX
+}  // namespace w128
 }  // namespace slbm
 
 #include <algorithm>
@@ -70,17 +76,19 @@ cudaError_t prepare_batch_kernels() {
     static PerDeviceOnce once;
     return once([] {
         const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        const int sm = (int)smem_bytes<T>(), sm32 = (int)w32::smem_bytes<T>();
+        const int sm = (int)smem_bytes<T>(), sm32 = (int)w32::smem_bytes<T>(), sm128 = (int)w128::smem_bytes<T>();
         cudaError_t e = cudaFuncSetAttribute(step_kernel<T, false, false, true>, attr, sm);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<T, false, true, true>, attr, sm);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(w32::step_kernel<T, false, false, true>, attr, sm32);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(w32::step_kernel<T, false, true, true>, attr, sm32);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(w128::step_kernel<T, false, false, true>, attr, sm128);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(w128::step_kernel<T, false, true, true>, attr, sm128);
         return e;
     });
 }
 
 // resident CTAs per SM the strip width allows at most (shared memory and registers)
-int max_ctas_per_sm(int width) { return width == 32 ? 3 : 2; }
+int max_ctas_per_sm(int width) { return width == 32 ? 3 : (width == 128 ? 1 : 2); }
 
 }  // namespace
 
@@ -191,6 +199,10 @@ cudaError_t launch_batch(slbm_batch* b) {
         const size_t sm = w32::smem_bytes<T>();
         if (b->var) w32::step_kernel<T, false, true, true><<<b->nctas, w32::NTHREADS, sm, b->stream>>>(a, ba, none);
         else w32::step_kernel<T, false, false, true><<<b->nctas, w32::NTHREADS, sm, b->stream>>>(a, ba, none);
+    } else if (b->strip_width == 128) {
+        const size_t sm = w128::smem_bytes<T>();
+        if (b->var) w128::step_kernel<T, false, true, true><<<b->nctas, w128::NTHREADS, sm, b->stream>>>(a, ba, none);
+        else w128::step_kernel<T, false, false, true><<<b->nctas, w128::NTHREADS, sm, b->stream>>>(a, ba, none);
     } else {
         const size_t sm = smem_bytes<T>();
         if (b->var) step_kernel<T, false, true, true><<<b->nctas, NTHREADS, sm, b->stream>>>(a, ba, none);
@@ -468,7 +480,7 @@ slbm_status slbm_batch_set_tiling(slbm_batch* b, int band_rows, int ctas_per_sm,
 
 slbm_status slbm_batch_set_strip_width(slbm_batch* b, int width) {
     if (!b) return SLBM_EINVAL;
-    if (width != 32 && width != 64) return bfail(b, SLBM_EINVAL, "strip width must be 32 or 64");
+    if (width != 32 && width != 64 && width != 128) return bfail(b, SLBM_EINVAL, "strip width must be 32, 64 or 128");
     b->strip_width = width;
     if (b->ctas_per_sm > max_ctas_per_sm(width)) b->ctas_per_sm = max_ctas_per_sm(width);
     b->tables_valid = false;
@@ -541,7 +553,7 @@ slbm_status slbm_batch_autotune(slbm_batch* b, const char* cache_path, int* band
             int br = 0, cs = 0, width = 64;
             char key[256] = {0};
             const int got = std::sscanf(line.c_str(), " \"%255[^\"]\": [%d, %d, %d]", key, &br, &cs, &width);
-            if (got >= 3 && sig == key && (width == 32 || width == 64)) {
+            if (got >= 3 && sig == key && (width == 32 || width == 64 || width == 128)) {
                 apply(width, br, cs);
                 return SLBM_OK;
             }
@@ -555,7 +567,7 @@ slbm_status slbm_batch_autotune(slbm_batch* b, const char* cache_path, int* band
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int width : {64, 32}) {
+    for (int width : {64, 32, 128}) {
         slbm_batch_set_strip_width(b, width);
         for (int cs = 1; cs <= max_ctas_per_sm(width); ++cs) {
             for (int br : bands) {
