@@ -243,11 +243,13 @@ __global__ void __launch_bounds__(T3) potentials3d(const Args3 A, int diag) {
 #pragma unroll
     for (int q = 0; q < NPART; ++q) acc[q] = {0.f, 0.f};
     float clamps = 0.f;
-    for_cells(G, [&](long long c, int x, int y, int z) {
+    // rows off the walls take a variant without the ghost-plane tests of the links
+    auto cell = [&](auto in_c, long long c, int x, int y, int z) {
+        constexpr bool IN = decltype(in_c)::value;
         const float2 pc = A.phi[c], sc = A.psi[c];
         const float phi = pc.x, psi = sc.x;
         float lgp = 0.f, lgs = 0.f, lnp = 0.f, lns = 0.f;
-        const bool wall = (y == 0 || y == G.ny - 1);
+        const bool wall = !IN && (y == 0 || y == G.ny - 1);
         const Nbr nb(G, c, x, y, z);
         sfor<1, Q3>([&](auto KI) {
             constexpr int k = decltype(KI)::value;
@@ -294,6 +296,10 @@ __global__ void __launch_bounds__(T3) potentials3d(const Args3 A, int diag) {
         acc[P_Q] = ff_add_f(acc[P_Q], 1.5f * u - 0.5f * u * u * u);
         acc[P_PHI] = ff_add(acc[P_PHI], {pc.x, pc.y});
         acc[P_PSI] = ff_add(acc[P_PSI], {sc.x, sc.y});
+    };
+    for_cells(G, [&](long long c, int x, int y, int z) {
+        if (y > 0 && y < G.ny - 1) cell(std::true_type{}, c, x, y, z);
+        else cell(std::false_type{}, c, x, y, z);
     });
     acc[P_CLAMP] = {clamps, 0.f};
     __shared__ double s_blk[NPART], s_tot[NPART];
